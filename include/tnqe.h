@@ -1,0 +1,146 @@
+/*
+ * tnqe.h -- C ABI of the GB300 (sm_103a) matrix-element library for the
+ * tensor-network quantum eigensolver of Leimkuhler & Whaley, arXiv 2404.10223.
+ *
+ * The wavefunction is a linear combination of M matrix product states (MPS),
+ * each in its own orbital basis (Eq. 8, Sec. II B).  The library fills the
+ * subspace matrices H_ij = <psi_i|H|psi_j> and S_ij = <psi_i|psi_j> (Eq. 10)
+ * for a list of pairs and solves H c = E S c (Eq. 9) by canonical
+ * orthogonalisation (Sec. IV C, App. A2).
+ *
+ * Conventions (fixed by this ABI):
+ *  - Spatial-orbital sites, local dimension d = 4, local index
+ *    k = n_alpha + 2 n_beta (Sec. II A lists vac, up, down, updown as
+ *    00, 01, 10, 11).  |k_0 ... k_{N-1}> = prod_p (a+_{p,alpha})^{n}(a+_{p,beta})^{n} |vac>
+ *    with p ascending; Jordan-Wigner order 0a, 0b, 1a, 1b, ...
+ *  - Hamiltonian (Eq. 1) in chemists' notation:
+ *    H = sum_{pq,s} h_pq a+_ps a_qs + 1/2 sum_{pqrs,st} (pq|rs) a+_ps a+_rt a_st a_qs.
+ *  - State j is psi_j = G(U_j) |MPS_j>, where G(V) a+_q G(V)^-1 = sum_p a+_p V_pq
+ *    and column p of U_j is orbital p of basis j in the reference orbitals.
+ *  - Pair (i, j) brings MPS_j into basis i with the Givens network of
+ *    V = U_i^T U_j (Eq. 11) and SVD truncation, then contracts
+ *    <MPS_i| H^(i) |G(V) MPS_j> against the MPO of H expressed in basis i.
+ *
+ * Memory: all input arrays are copied; the caller keeps ownership.  Output
+ * arrays may live in host or device memory (detected per pointer).  Every
+ * call returns a status; no exception, exit or abort crosses the ABI.  A
+ * context is not thread-safe: use one context per host thread.
+ */
+#ifndef TNQE_H
+#define TNQE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tnqe_ctx tnqe_ctx;
+
+typedef enum {
+  TNQE_OK = 0,
+  TNQE_ERR_ARG = 1,      /* invalid argument (sizes, non-orthogonal U, broken MPS form) */
+  TNQE_ERR_STATE = 2,    /* call out of order (e.g. unknown MPS id) */
+  TNQE_ERR_NOMEM = 3,    /* device or host allocation failed */
+  TNQE_ERR_CUDA = 4,     /* a CUDA runtime call failed */
+  TNQE_ERR_NOCONV = 5,   /* a Jacobi iteration hit its sweep limit (results still written) */
+  TNQE_ERR_TIMEOUT = 6,  /* a bounded device wait gave up */
+  TNQE_ERR_NUMERIC = 7   /* NaN/Inf in an output */
+} tnqe_status;
+
+typedef enum {
+  TNQE_PREC_FP64 = 0,    /* every step in FP64 */
+  TNQE_PREC_TF32X3 = 1,  /* transfer contractions as 3-term split TF32 products, FP32 accumulation */
+  TNQE_PREC_BF16X3 = 2   /* transfer contractions as 3-term split BF16 products, FP32 accumulation */
+} tnqe_precision;
+
+typedef struct {
+  int precision;            /* tnqe_precision; the rotation SVDs and the solve are FP64 always */
+  int chi_rot;              /* bond-dimension cap of a rotated state; 0 = max bond dim of MPS j */
+  double cutoff;            /* keep sigma_l > cutoff * sigma_1 (relative singular-value threshold) */
+  double solve_eps;         /* keep eigenvalues of S above solve_eps * lambda_max */
+  int renormalize_rotated;  /* 1: rescale a rotated state to its pre-rotation norm (App. A1) */
+  int max_jacobi_sweeps;    /* Jacobi sweep limit (SVD and eigensolver) */
+  long long max_spin;       /* iteration limit of any device-side wait */
+  void* cuda_stream;        /* cudaStream_t to launch on; NULL = a stream owned by the context */
+  int device;               /* CUDA device ordinal */
+} tnqe_options;
+
+/* Fill *opt with defaults: FP64, chi_rot 0, cutoff 1e-14, solve_eps 1e-10,
+ * no renormalisation, 60 Jacobi sweeps, max_spin 1<<26, own stream, device 0. */
+void tnqe_default_options(tnqe_options* opt);
+
+/* Create a context for N spatial orbitals and (n_alpha, n_beta) electrons.
+ * h1: N*N row-major, symmetric.  eri: N^4 row-major (pq|rs).  Both copied.
+ * Requires 1 <= N <= 32 and n_alpha, n_beta <= 14.  opt may be NULL.
+ * On success *out owns all device memory of the context. */
+tnqe_status tnqe_create(const double* h1, const double* eri, int N, int n_alpha, int n_beta,
+                        const tnqe_options* opt, tnqe_ctx** out);
+
+/* Add one state (Eq. 3).  tensors[s] points to site s, shape
+ * [bond_dims[s]][4][bond_dims[s+1]] row-major FP64 (host memory).
+ * bond_dims has N+1 entries, bond_dims[0] = bond_dims[N] = 1.
+ * U: N*N row-major orthogonal (|U^T U - I|_max < 1e-12).
+ * The MPS must be left-orthonormal on sites 0..N-2 (canonical centre on the
+ * last site, Eq. A3) to 1e-10, and every bond index must carry a definite
+ * (n_alpha, n_beta) charge: A[l,k,r] may be nonzero (above 1e-12 of the
+ * site's largest entry) only when q(l) + q(k) = q(r), with the last bond at
+ * (n_alpha, n_beta).  Violations return TNQE_ERR_ARG.  Builds the Hamiltonian
+ * MPO in basis U on the host and uploads tensors and MPO. */
+tnqe_status tnqe_add_mps(tnqe_ctx* ctx, const double* const* tensors, const int* bond_dims,
+                         const double* U, int* mps_id);
+
+/* Drop every state (device buffers are kept for reuse by later adds). */
+tnqe_status tnqe_reset_mps(tnqe_ctx* ctx);
+
+/* Rotate MPS j into basis i (Eq. 11 with truncation, Sec. II D) and keep the
+ * result for tnqe_get_rotated.  *discarded_weight (host, may be NULL) gets the
+ * sum of squared discarded singular values over all gates. */
+tnqe_status tnqe_rotate(tnqe_ctx* ctx, int i, int j, double* discarded_weight);
+
+/* Copy the state kept by the last tnqe_rotate to host memory.  bond_dims gets
+ * N+1 ints; tensors gets the sites back to back ([chi_s][4][chi_{s+1}] each)
+ * and must hold max_doubles values; returns TNQE_ERR_ARG if it is too small. */
+tnqe_status tnqe_get_rotated(tnqe_ctx* ctx, int* bond_dims, double* tensors, long long max_doubles);
+
+/* H_ij and S_ij (Eq. 10) for npairs pairs.  pairs: 2*npairs ints (host),
+ * (i, j) with i <= j.  H_out, S_out: npairs doubles each, host or device.
+ * Every pair is recomputed (rotation and contraction) on each call. */
+tnqe_status tnqe_matrix_elements(tnqe_ctx* ctx, const int* pairs, int npairs,
+                                 double* H_out, double* S_out);
+
+/* Generalized eigenproblem H c = E S c (Eq. 9) for M <= 32 by canonical
+ * orthogonalisation (projection method, Sec. IV C), on the GPU in FP64.
+ * H, S: M*M row-major, host; the upper triangle (i <= j) is used.
+ * E: M doubles, the rank_kept ascending eigenvalues first, the rest NaN.
+ * C: M*M row-major, column k = eigenvector k (C^T S C = I), zero beyond rank.
+ * kappa1 = |c_1|^2 / sqrt(E_1^2 + 1) (App. A2).  Outputs are host memory. */
+tnqe_status tnqe_solve(tnqe_ctx* ctx, const double* H, const double* S, int M,
+                       double* E, double* C, int* rank_kept, double* kappa1);
+
+/* Change the contraction precision (tnqe_precision) of later calls. */
+tnqe_status tnqe_set_precision(tnqe_ctx* ctx, int precision);
+
+/* Device time (ms) of the phases of the last tnqe_matrix_elements call,
+ * measured with CUDA events on the context stream:
+ * times[0] rotation, times[1] contraction, times[2] whole call.
+ * launches: number of kernels that call launched. */
+tnqe_status tnqe_last_timing(const tnqe_ctx* ctx, double* times, int* launches);
+
+/* Per-kernel profile of the last tnqe_matrix_elements call (n values written, n <= 10):
+ * [0] rotation kernel ms, [1] stage-1 GEMM ms (X = L B), [2] stage-2 MPO ms,
+ * [3] stage-3 GEMM ms (L' = A^T Y), [4] rotation algorithmic FLOPs
+ * (two-site contraction + gate + 4mn^2 + 8n^3 per SVD block), [5] stage-1 FLOPs,
+ * [6] stage-2 algorithmic bytes (X read once, Y written once), [7] stage-3 FLOPs,
+ * [8] stage-2 FLOPs, [9] kernels launched.  Times come from CUDA events on the
+ * context stream around each launch and are summed over sites. */
+tnqe_status tnqe_last_profile(const tnqe_ctx* ctx, double* prof, int n);
+
+/* Human-readable description of the last error on this context. */
+const char* tnqe_last_error(const tnqe_ctx* ctx);
+
+/* Release the context and all its device memory. */
+void tnqe_destroy(tnqe_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TNQE_H */

@@ -1,0 +1,983 @@
+// C ABI (include/tnqe.h): context, validation, host planning, device memory and
+// the launch sequence of the matrix-element path.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "../../include/tnqe.h"
+#include "internal.h"
+
+using namespace tnqe;
+
+namespace {
+
+struct Error : std::runtime_error {
+  tnqe_status st;
+  Error(tnqe_status s, const std::string& m) : std::runtime_error(m), st(s) {}
+};
+
+#define CK(call)                                                                                      \
+  do {                                                                                                \
+    cudaError_t e_ = (call);                                                                          \
+    if (e_ != cudaSuccess)                                                                            \
+      throw Error(e_ == cudaErrorMemoryAllocation ? TNQE_ERR_NOMEM : TNQE_ERR_CUDA,                    \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                               \
+  } while (0)
+#define CKL(call)                                                                                     \
+  do {                                                                                                \
+    int e_ = (call);                                                                                  \
+    if (e_ != 0) throw Error(TNQE_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString((cudaError_t)e_)); \
+  } while (0)
+
+// device allocation that grows on demand and is kept for reuse
+struct DBuf {
+  void* p = nullptr;
+  size_t cap = 0;
+  void ensure(size_t bytes) {
+    if (bytes <= cap) return;
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+    size_t b = std::max<size_t>(bytes, 256);
+    CK(cudaMalloc(&p, b));
+    cap = b;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+  }
+  template <class T> T* as() const { return reinterpret_cast<T*>(p); }
+};
+
+template <class T> T* dalloc_copy(const std::vector<T>& v, std::vector<void*>& owned) {
+  void* p = nullptr;
+  CK(cudaMalloc(&p, std::max<size_t>(v.size() * sizeof(T), 16)));
+  if (!v.empty()) CK(cudaMemcpy(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+  owned.push_back(p);
+  return reinterpret_cast<T*>(p);
+}
+
+double binom(int n, int k) {
+  if (k < 0 || k > n) return 0.0;
+  double r = 1.0;
+  for (int i = 1; i <= k; ++i) r = r * (n - k + i) / i;
+  return r;
+}
+
+struct DevMps {
+  std::vector<int> dims;                 // N + 1
+  std::vector<SectorTable> sec;          // N + 1
+  std::vector<long long> off;            // N
+  std::vector<double> U;
+  int chi = 1;
+  double* d_t = nullptr;
+  long long* d_off = nullptr;
+  int* d_dims = nullptr;
+  SectorTable* d_sec = nullptr;
+  Mpo mpo;                               // host copy (dims, CSR)
+  std::vector<int*> d_rowptr, d_col;
+  std::vector<double*> d_val;
+  std::vector<void*> owned;
+  void free_all() {
+    for (void* p : owned) cudaFree(p);
+    owned.clear();
+  }
+};
+
+struct PairPlan {                        // cached per (i, j): Givens gates on the device
+  int ngates = 0, neg_site = -1;
+  double* d_gates = nullptr;
+  int* d_site = nullptr;
+  int* d_side = nullptr;
+  std::vector<void*> owned;
+};
+
+}  // namespace
+
+struct tnqe_ctx {
+  tnqe_options opt{};
+  int N = 0, na = 0, nb = 0;
+  std::vector<double> h1, eri;
+  std::vector<int> exact_dim;            // N + 1: full sector-space dimension per bond
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::vector<std::unique_ptr<DevMps>> mps;
+  std::map<std::pair<int, int>, std::unique_ptr<PairPlan>> plans;
+  std::string err;
+  // rotation workspace
+  DBuf rot_work, rot_scratch, rot_meta, rot_small, rot_desc;
+  // contraction workspace
+  DBuf con_ws, con_desc, con_out;
+  // last tnqe_rotate result
+  int kept_pair_valid = 0;
+  std::vector<int> kept_dims;
+  std::vector<long long> kept_off;
+  double times[3] = {0, 0, 0};
+  int launches = 0;
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  // per-kernel profile of the last matrix-element call (see tnqe_last_profile)
+  std::vector<cudaEvent_t> pev;
+  double prof[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+};
+
+namespace {
+
+tnqe_status fail(tnqe_ctx* c, const Error& e) {
+  if (c) c->err = e.what();
+  return e.st;
+}
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// ----------------------------------------------------------------------------- rotation of a batch
+struct RotBatch {
+  std::vector<int> pair_idx;             // index into the caller's pair list
+  std::vector<int> ii, jj;
+  std::vector<std::vector<int>> cap;     // per pair: N + 1 capacities
+  std::vector<std::vector<long long>> woff;
+  std::vector<long long> work_base;      // doubles, per pair
+  std::vector<long long> scratch_base;   // doubles, per pair (theta + wbuf + qbuf)
+  std::vector<long long> scratch_len;
+  // device views per pair
+  std::vector<double*> work;
+  std::vector<int*> dims;
+  std::vector<SectorTable*> sec;
+  std::vector<double*> disc;
+  std::vector<int*> status;
+  std::vector<double*> flops;
+};
+
+const long long META_INTS = 2 * 32768;
+
+PairPlan* get_plan(tnqe_ctx* c, int i, int j) {
+  auto key = std::make_pair(i, j);
+  auto it = c->plans.find(key);
+  if (it != c->plans.end()) return it->second.get();
+  const int N = c->N;
+  const std::vector<double>& Ui = c->mps[i]->U;
+  const std::vector<double>& Uj = c->mps[j]->U;
+  std::vector<double> V((size_t)N * N);
+  for (int p = 0; p < N; ++p)
+    for (int q = 0; q < N; ++q) {
+      double acc = 0.0;
+      for (int a = 0; a < N; ++a) acc += Ui[(size_t)a * N + p] * Uj[(size_t)a * N + q];
+      V[(size_t)p * N + q] = acc;
+    }
+  GivensPlan gp = givens_plan(V.data(), N);
+  auto pp = std::make_unique<PairPlan>();
+  pp->ngates = (int)gp.gates.size();
+  pp->neg_site = gp.neg_site;
+  std::vector<double> G((size_t)std::max(1, pp->ngates) * 256, 0.0);
+  std::vector<int> site(std::max(1, pp->ngates)), side(std::max(1, pp->ngates));
+  for (int g = 0; g < pp->ngates; ++g) {
+    gate_matrix(gp.gates[g].c, gp.gates[g].s, &G[(size_t)g * 256]);
+    site[g] = gp.gates[g].site;
+    side[g] = gp.gates[g].side;
+  }
+  pp->d_gates = dalloc_copy(G, pp->owned);
+  pp->d_site = dalloc_copy(site, pp->owned);
+  pp->d_side = dalloc_copy(side, pp->owned);
+  PairPlan* raw = pp.get();
+  c->plans.emplace(key, std::move(pp));
+  return raw;
+}
+
+int chi_rot_of(tnqe_ctx* c, int j) { return c->opt.chi_rot > 0 ? c->opt.chi_rot : c->mps[j]->chi; }
+
+// Launch the rotation of every (i, j), i != j, of `pairs`; results stay in rot_work.
+void run_rotations(tnqe_ctx* c, const std::vector<std::pair<int, int>>& pairs, RotBatch& rb) {
+  const int N = c->N;
+  rb = RotBatch{};
+  for (size_t p = 0; p < pairs.size(); ++p)
+    if (pairs[p].first != pairs[p].second) {
+      rb.pair_idx.push_back((int)p);
+      rb.ii.push_back(pairs[p].first);
+      rb.jj.push_back(pairs[p].second);
+    }
+  const int np = (int)rb.pair_idx.size();
+  if (np == 0) return;
+  long long work_total = 0, scratch_total = 0;
+  for (int k = 0; k < np; ++k) {
+    const DevMps& mj = *c->mps[rb.jj[k]];
+    const int cr = chi_rot_of(c, rb.jj[k]);
+    std::vector<int> cap(N + 1);
+    for (int b = 0; b <= N; ++b) cap[b] = std::max(std::min(cr, c->exact_dim[b]), mj.dims[b]);
+    if (*std::max_element(cap.begin(), cap.end()) > 256)
+      throw Error(TNQE_ERR_ARG, "bond dimension above 256 is not supported by the rotation kernel");
+    std::vector<long long> off(N);
+    long long tot = 0;
+    for (int s = 0; s < N; ++s) {
+      off[s] = tot;
+      tot += (long long)cap[s] * 4 * cap[s + 1];
+    }
+    long long th = 16;
+    for (int a = 0; a + 1 < N; ++a) th = std::max(th, 16LL * cap[a] * cap[a + 2]);
+    rb.cap.push_back(cap);
+    rb.woff.push_back(off);
+    rb.work_base.push_back(work_total);
+    work_total += tot;
+    rb.scratch_base.push_back(scratch_total);
+    rb.scratch_len.push_back(th);
+    scratch_total += 3 * th;
+  }
+  // small per-pair arrays: dims (N+1 ints), caps, offsets, sectors, disc, status
+  auto al256 = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  const size_t sec_bytes = al256(sizeof(SectorTable) * (N + 1));
+  const size_t per_small = al256(sec_bytes + 2 * 256 + (size_t)(N + 1) * 8 * 2 + (size_t)N * 8 + 64);
+  c->rot_work.ensure(sizeof(double) * std::max<long long>(work_total, 1));
+  c->rot_scratch.ensure(sizeof(double) * std::max<long long>(scratch_total, 1));
+  c->rot_meta.ensure(sizeof(int) * META_INTS * np);
+  c->rot_small.ensure(per_small * np);
+  c->rot_desc.ensure(sizeof(RotDesc) * np);
+  std::vector<unsigned char> small(per_small * np, 0);
+  std::vector<RotDesc> descs(np);
+  for (int k = 0; k < np; ++k) {
+    unsigned char* hb = small.data() + per_small * k;
+    unsigned char* db = c->rot_small.as<unsigned char>() + per_small * k;
+    size_t o = 0;
+    SectorTable* dsec = reinterpret_cast<SectorTable*>(db + o);
+    o += sec_bytes;
+    int* ddims = reinterpret_cast<int*>(db + o);
+    o += 256;
+    int* dcap = reinterpret_cast<int*>(db + o);
+    std::memcpy(hb + o, rb.cap[k].data(), sizeof(int) * (N + 1));
+    o += 256;
+    long long* dwoff = reinterpret_cast<long long*>(db + o);
+    std::memcpy(hb + o, rb.woff[k].data(), sizeof(long long) * N);
+    o += (size_t)(N + 1) * 8 * 2 + (size_t)N * 8;
+    double* ddisc = reinterpret_cast<double*>(db + o);
+    double* dflops = reinterpret_cast<double*>(db + o + 8);
+    o += 16;
+    int* dstat = reinterpret_cast<int*>(db + o);
+    const DevMps& mj = *c->mps[rb.jj[k]];
+    PairPlan* pl = get_plan(c, rb.ii[k], rb.jj[k]);
+    RotDesc& d = descs[k];
+    d.N = N;
+    d.chi_rot = chi_rot_of(c, rb.jj[k]);
+    d.ngates = pl->ngates;
+    d.neg_site = pl->neg_site;
+    d.renorm = c->opt.renormalize_rotated;
+    d.max_sweeps = c->opt.max_jacobi_sweeps;
+    d.cutoff = c->opt.cutoff;
+    d.src = mj.d_t;
+    d.src_off = mj.d_off;
+    d.src_dims = mj.d_dims;
+    d.src_sec = mj.d_sec;
+    d.work = c->rot_work.as<double>() + rb.work_base[k];
+    d.work_off = dwoff;
+    d.work_dims = ddims;
+    d.work_cap = dcap;
+    d.work_sec = dsec;
+    d.gates = pl->d_gates;
+    d.gate_site = pl->d_site;
+    d.gate_side = pl->d_side;
+    double* sb = c->rot_scratch.as<double>() + rb.scratch_base[k];
+    d.theta = sb;
+    d.wbuf = sb + rb.scratch_len[k];
+    d.qbuf = sb + 2 * rb.scratch_len[k];
+    d.meta = c->rot_meta.as<int>() + META_INTS * k;
+    d.meta_cap = META_INTS;
+    d.discarded = ddisc;
+    d.status = dstat;
+    d.flops = dflops;
+    rb.work.push_back(d.work);
+    rb.dims.push_back(ddims);
+    rb.sec.push_back(dsec);
+    rb.disc.push_back(ddisc);
+    rb.status.push_back(dstat);
+    rb.flops.push_back(dflops);
+  }
+  CK(cudaMemcpyAsync(c->rot_small.p, small.data(), small.size(), cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemcpyAsync(c->rot_desc.p, descs.data(), sizeof(RotDesc) * np, cudaMemcpyHostToDevice, c->stream));
+  CK(cudaEventRecord(c->pev[0], c->stream));
+  CKL(launch_rotate(c->rot_desc.as<RotDesc>(), np, 0, c->stream));
+  CK(cudaEventRecord(c->pev[1], c->stream));
+  c->launches += 1;
+}
+
+// read back dims / discarded / status of a finished rotation batch
+void fetch_rotation_results(tnqe_ctx* c, const RotBatch& rb, std::vector<std::vector<int>>& dims,
+                            std::vector<double>& disc, int& status_or) {
+  const int N = c->N;
+  const int np = (int)rb.pair_idx.size();
+  dims.assign(np, std::vector<int>(N + 1));
+  disc.assign(np, 0.0);
+  status_or = 0;
+  for (int k = 0; k < np; ++k) {
+    CK(cudaMemcpyAsync(dims[k].data(), rb.dims[k], sizeof(int) * (N + 1), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(&disc[k], rb.disc[k], sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  }
+  std::vector<int> st(np);
+  std::vector<double> fl(np);
+  for (int k = 0; k < np; ++k) {
+    CK(cudaMemcpyAsync(&st[k], rb.status[k], sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(&fl[k], rb.flops[k], sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  }
+  CK(cudaStreamSynchronize(c->stream));
+  for (int k = 0; k < np; ++k) {
+    status_or |= st[k];
+    c->prof[4] += fl[k];
+  }
+  float ms = 0.f;
+  CK(cudaEventElapsedTime(&ms, c->pev[0], c->pev[1]));
+  c->prof[0] += ms;
+}
+
+// ----------------------------------------------------------------------------- contraction
+struct KetView {
+  const double* base;
+  std::vector<long long> off;   // per site
+  std::vector<int> dims;        // N + 1
+};
+
+void run_contractions(tnqe_ctx* c, const std::vector<std::pair<int, int>>& pairs, const std::vector<KetView>& kets,
+                      double* d_H, double* d_S) {
+  const int N = c->N;
+  const int np = (int)pairs.size();
+  // workspace per pair: two environments, X and Y
+  std::vector<long long> envsz(np), xsz(np), ysz(np);
+  for (int p = 0; p < np; ++p) {
+    const DevMps& bi = *c->mps[pairs[p].first];
+    const KetView& kv = kets[p];
+    long long e = 1, x = 1, y = 1;
+    for (int t = 0; t <= N; ++t) e = std::max(e, (long long)bi.dims[t] * bi.mpo.dims[t] * kv.dims[t]);
+    for (int t = 0; t < N; ++t) {
+      x = std::max(x, (long long)bi.dims[t] * bi.mpo.dims[t] * 4 * kv.dims[t + 1]);
+      y = std::max(y, (long long)bi.dims[t] * 4 * bi.mpo.dims[t + 1] * kv.dims[t + 1]);
+    }
+    envsz[p] = e;
+    xsz[p] = x;
+    ysz[p] = y;
+  }
+  size_t freeb = 0, totalb = 0;
+  CK(cudaMemGetInfo(&freeb, &totalb));
+  const double budget = 0.6 * (double)(freeb + c->con_ws.cap);
+  // waves of pairs whose workspace fits
+  size_t p0 = 0;
+  while (p0 < (size_t)np) {
+    size_t p1 = p0;
+    double need = 0.0;
+    while (p1 < (size_t)np) {
+      const double add = 8.0 * (2.0 * envsz[p1] + xsz[p1] + ysz[p1]);
+      if (p1 > p0 && need + add > budget) break;
+      need += add;
+      ++p1;
+    }
+    const int nw = (int)(p1 - p0);
+    c->con_ws.ensure((size_t)need + 256);
+    std::vector<double*> env0(nw), env1(nw), X(nw), Y(nw);
+    {
+      double* base = c->con_ws.as<double>();
+      long long o = 0;
+      for (int w = 0; w < nw; ++w) {
+        const int p = (int)p0 + w;
+        env0[w] = base + o;
+        o += envsz[p];
+        env1[w] = base + o;
+        o += envsz[p];
+        X[w] = base + o;
+        o += xsz[p];
+        Y[w] = base + o;
+        o += ysz[p];
+      }
+    }
+    // descriptors for all sites of this wave
+    std::vector<GemmDesc> g1, g3;
+    std::vector<SpmmDesc> sp;
+    std::vector<long long> g1pre, g3pre, sppre;
+    std::vector<int> g1n, g3n, spn;
+    for (int t = 0; t < N; ++t) {
+      long long tiles1 = 0, tiles3 = 0, rows = 0;
+      int n1 = 0, n3 = 0, ns = 0;
+      for (int w = 0; w < nw; ++w) {
+        const int p = (int)p0 + w;
+        const DevMps& bi = *c->mps[pairs[p].first];
+        const KetView& kv = kets[p];
+        const int ca = bi.dims[t], ca2 = bi.dims[t + 1];
+        const int cb = kv.dims[t], cb2 = kv.dims[t + 1];
+        const int Din = bi.mpo.dims[t], Dout = bi.mpo.dims[t + 1];
+        double* Lin = (t & 1) ? env1[w] : env0[w];
+        double* Lout = (t & 1) ? env0[w] : env1[w];
+        GemmDesc d1{};
+        d1.M = ca * Din;
+        d1.N = 4 * cb2;
+        d1.K = cb;
+        d1.transA = 0;
+        d1.lda = cb;
+        d1.ldb = 4 * cb2;
+        d1.ldc = 4 * cb2;
+        d1.A = Lin;
+        d1.B = kv.base + kv.off[t];
+        d1.C = X[w];
+        g1pre.push_back(tiles1);
+        tiles1 += (long long)((d1.M + 63) / 64) * ((d1.N + 63) / 64);
+        g1.push_back(d1);
+        ++n1;
+        SpmmDesc s{};
+        s.chi_a = ca;
+        s.nrows = 4 * Dout;
+        s.ncols_x = 4 * Din;
+        s.width = cb2;
+        s.rowptr = bi.d_rowptr[t];
+        s.col = bi.d_col[t];
+        s.val = bi.d_val[t];
+        s.X = X[w];
+        s.Y = Y[w];
+        sppre.push_back(rows);
+        rows += (long long)ca * 4 * Dout;
+        sp.push_back(s);
+        ++ns;
+        GemmDesc d3{};
+        d3.M = ca2;
+        d3.N = Dout * cb2;
+        d3.K = 4 * ca;
+        d3.transA = 1;
+        d3.lda = ca2;
+        d3.ldb = Dout * cb2;
+        d3.ldc = Dout * cb2;
+        d3.A = bi.d_t + bi.off[t];
+        d3.B = Y[w];
+        d3.C = Lout;
+        g3pre.push_back(tiles3);
+        tiles3 += (long long)((d3.M + 63) / 64) * ((d3.N + 63) / 64);
+        g3.push_back(d3);
+        ++n3;
+      }
+      g1pre.push_back(tiles1);
+      g3pre.push_back(tiles3);
+      sppre.push_back(rows);
+      g1n.push_back(n1);
+      g3n.push_back(n3);
+      spn.push_back(ns);
+    }
+    // pack descriptors + prefixes into one upload
+    const size_t b1 = g1.size() * sizeof(GemmDesc), b3 = g3.size() * sizeof(GemmDesc), bs = sp.size() * sizeof(SpmmDesc);
+    const size_t bp1 = g1pre.size() * 8, bp3 = g3pre.size() * 8, bps = sppre.size() * 8;
+    const size_t bf = (size_t)nw * sizeof(double*);
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    const size_t total = al(b1) + al(b3) + al(bs) + al(bp1) + al(bp3) + al(bps) + al(bf);
+    std::vector<unsigned char> host(total, 0);
+    size_t o1 = 0, o3 = o1 + al(b1), os = o3 + al(b3), op1 = os + al(bs), op3 = op1 + al(bp1), ops = op3 + al(bp3),
+           of = ops + al(bps);
+    std::memcpy(host.data() + o1, g1.data(), b1);
+    std::memcpy(host.data() + o3, g3.data(), b3);
+    std::memcpy(host.data() + os, sp.data(), bs);
+    std::memcpy(host.data() + op1, g1pre.data(), bp1);
+    std::memcpy(host.data() + op3, g3pre.data(), bp3);
+    std::memcpy(host.data() + ops, sppre.data(), bps);
+    std::vector<const double*> fin(nw);
+    for (int w = 0; w < nw; ++w) fin[w] = (N & 1) ? env1[w] : env0[w];
+    std::memcpy(host.data() + of, fin.data(), bf);
+    c->con_desc.ensure(total);
+    unsigned char* dd = c->con_desc.as<unsigned char>();
+    CK(cudaMemcpyAsync(dd, host.data(), total, cudaMemcpyHostToDevice, c->stream));
+    // L_0 = 1 for every pair of the wave
+    {
+      const double one = 1.0;
+      for (int w = 0; w < nw; ++w)
+        CK(cudaMemcpyAsync(env0[w], &one, sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    }
+    for (const GemmDesc& d : g1) c->prof[5] += 2.0 * d.M * d.N * d.K;
+    for (const GemmDesc& d : g3) c->prof[7] += 2.0 * d.M * d.N * d.K;
+    for (int w = 0; w < nw; ++w) {
+      const int p = (int)p0 + w;
+      const DevMps& bi = *c->mps[pairs[p].first];
+      const KetView& kv = kets[p];
+      for (int t = 0; t < N; ++t) {
+        const double ca = bi.dims[t], cb2 = kv.dims[t + 1];
+        c->prof[6] += 8.0 * ca * cb2 * 4.0 * (bi.mpo.dims[t] + bi.mpo.dims[t + 1]);
+        c->prof[8] += 2.0 * (double)bi.mpo.sites[t].val.size() * ca * cb2;
+      }
+    }
+    size_t i1 = 0, i3 = 0, is = 0, ip1 = 0, ip3 = 0, ips = 0;
+    for (int t = 0; t < N; ++t) {
+      const int n1 = g1n[t], n3 = g3n[t], ns = spn[t];
+      cudaEvent_t* E = &c->pev[2 + 4 * t];
+      CK(cudaEventRecord(E[0], c->stream));
+      CKL(launch_gemm_f64(reinterpret_cast<GemmDesc*>(dd + o1) + i1, reinterpret_cast<long long*>(dd + op1) + ip1,
+                          n1, g1pre[ip1 + n1], c->stream));
+      CK(cudaEventRecord(E[1], c->stream));
+      CKL(launch_spmm_f64(reinterpret_cast<SpmmDesc*>(dd + os) + is, reinterpret_cast<long long*>(dd + ops) + ips,
+                          ns, sppre[ips + ns], c->stream));
+      CK(cudaEventRecord(E[2], c->stream));
+      CKL(launch_gemm_f64(reinterpret_cast<GemmDesc*>(dd + o3) + i3, reinterpret_cast<long long*>(dd + op3) + ip3,
+                          n3, g3pre[ip3 + n3], c->stream));
+      CK(cudaEventRecord(E[3], c->stream));
+      c->launches += 3;
+      i1 += n1;
+      i3 += n3;
+      is += ns;
+      ip1 += n1 + 1;
+      ip3 += n3 + 1;
+      ips += ns + 1;
+    }
+    CKL(launch_extract(reinterpret_cast<const double* const*>(dd + of), nw, d_H + p0, d_S + p0, c->stream));
+    c->launches += 1;
+    CK(cudaStreamSynchronize(c->stream));   // the next wave reuses the workspace and the events
+    for (int t = 0; t < N; ++t) {
+      cudaEvent_t* E = &c->pev[2 + 4 * t];
+      float a = 0.f, b = 0.f, d = 0.f;
+      CK(cudaEventElapsedTime(&a, E[0], E[1]));
+      CK(cudaEventElapsedTime(&b, E[1], E[2]));
+      CK(cudaEventElapsedTime(&d, E[2], E[3]));
+      c->prof[1] += a;
+      c->prof[2] += b;
+      c->prof[3] += d;
+    }
+    p0 = p1;
+  }
+}
+
+void check_ctx(tnqe_ctx* c) {
+  if (!c) throw Error(TNQE_ERR_ARG, "null context");
+  CK(cudaSetDevice(c->opt.device));
+}
+
+// ----------------------------------------------------------------------------- add_mps validation
+void prepare_mps(tnqe_ctx* c, const double* const* tensors, const int* bond_dims, const double* U, DevMps& m) {
+  const int N = c->N;
+  if (!tensors || !bond_dims || !U) throw Error(TNQE_ERR_ARG, "null argument");
+  if (bond_dims[0] != 1 || bond_dims[N] != 1) throw Error(TNQE_ERR_ARG, "bond_dims[0] and bond_dims[N] must be 1");
+  for (int b = 0; b <= N; ++b)
+    if (bond_dims[b] < 1 || bond_dims[b] > 256) throw Error(TNQE_ERR_ARG, "bond dimensions must be in [1, 256]");
+  // U orthogonal
+  for (int p = 0; p < N; ++p)
+    for (int q = 0; q < N; ++q) {
+      double acc = 0.0;
+      for (int a = 0; a < N; ++a) acc += U[(size_t)a * N + p] * U[(size_t)a * N + q];
+      if (std::fabs(acc - (p == q ? 1.0 : 0.0)) > 1e-12) throw Error(TNQE_ERR_ARG, "U is not orthogonal to 1e-12");
+    }
+  m.U.assign(U, U + (size_t)N * N);
+  // charges of every bond index, left to right
+  std::vector<std::vector<int>> q(N + 1);
+  q[0] = {0};
+  for (int s = 0; s < N; ++s) {
+    const int cl = bond_dims[s], cr = bond_dims[s + 1];
+    const double* A = tensors[s];
+    if (!A) throw Error(TNQE_ERR_ARG, "null site tensor");
+    double amax = 0.0;
+    for (long long x = 0; x < (long long)cl * 4 * cr; ++x) amax = std::max(amax, std::fabs(A[x]));
+    const double tol = 1e-12 * amax;
+    q[s + 1].assign(cr, -1);
+    for (int r = 0; r < cr; ++r) {
+      for (int l = 0; l < cl && q[s + 1][r] < 0; ++l)
+        for (int k = 0; k < 4; ++k)
+          if (std::fabs(A[((size_t)l * 4 + k) * cr + r]) > tol) {
+            const int qa = q[s][l] / QSTRIDE + (k & 1), qb = q[s][l] % QSTRIDE + (k >> 1);
+            q[s + 1][r] = qa * QSTRIDE + qb;
+            break;
+          }
+      if (q[s + 1][r] < 0) throw Error(TNQE_ERR_ARG, "site " + std::to_string(s) + ": bond index with no weight");
+      for (int l = 0; l < cl; ++l)
+        for (int k = 0; k < 4; ++k) {
+          const double v = A[((size_t)l * 4 + k) * cr + r];
+          const int qa = q[s][l] / QSTRIDE + (k & 1), qb = q[s][l] % QSTRIDE + (k >> 1);
+          if (std::fabs(v) > tol && qa * QSTRIDE + qb != q[s + 1][r])
+            throw Error(TNQE_ERR_ARG, "site " + std::to_string(s) + ": entry breaks the particle-number block structure");
+        }
+    }
+  }
+  if (q[N][0] != c->na * QSTRIDE + c->nb) throw Error(TNQE_ERR_ARG, "state is not in the (n_alpha, n_beta) sector");
+  // left-orthonormal sites 0..N-2 (columns of different charge have disjoint support)
+  for (int s = 0; s + 1 < N; ++s) {
+    const int cl = bond_dims[s], cr = bond_dims[s + 1];
+    const double* A = tensors[s];
+    for (int r1 = 0; r1 < cr; ++r1)
+      for (int r2 = r1; r2 < cr; ++r2) {
+        if (q[s + 1][r1] != q[s + 1][r2]) continue;
+        double acc = 0.0;
+        for (int lk = 0; lk < cl * 4; ++lk) acc += A[(size_t)lk * cr + r1] * A[(size_t)lk * cr + r2];
+        if (std::fabs(acc - (r1 == r2 ? 1.0 : 0.0)) > 1e-10)
+          throw Error(TNQE_ERR_ARG, "site " + std::to_string(s) + " is not left-orthonormal");
+      }
+  }
+  // sort every bond by charge (a gauge change: the state is unchanged)
+  std::vector<std::vector<int>> perm(N + 1);
+  m.dims.assign(bond_dims, bond_dims + N + 1);
+  m.sec.assign(N + 1, SectorTable{});
+  m.chi = *std::max_element(bond_dims, bond_dims + N + 1);
+  for (int b = 0; b <= N; ++b) {
+    perm[b].resize(bond_dims[b]);
+    for (int x = 0; x < bond_dims[b]; ++x) perm[b][x] = x;
+    std::stable_sort(perm[b].begin(), perm[b].end(), [&](int x, int y) { return q[b][x] < q[b][y]; });
+    SectorTable& T = m.sec[b];
+    T.nsec = 0;
+    for (int x = 0; x < bond_dims[b]; ++x) {
+      const int qq = q[b][perm[b][x]];
+      if (T.nsec == 0 || T.q[T.nsec - 1] != qq) {
+        if (T.nsec >= MAXSEC) throw Error(TNQE_ERR_ARG, "too many charge sectors on one bond");
+        T.q[T.nsec] = qq;
+        T.off[T.nsec] = x;
+        T.dim[T.nsec] = 0;
+        ++T.nsec;
+      }
+      ++T.dim[T.nsec - 1];
+    }
+  }
+  std::vector<double> host;
+  m.off.assign(N, 0);
+  for (int s = 0; s < N; ++s) {
+    const int cl = bond_dims[s], cr = bond_dims[s + 1];
+    m.off[s] = (long long)host.size();
+    const double* A = tensors[s];
+    const size_t base = host.size();
+    host.resize(base + (size_t)cl * 4 * cr);
+    for (int l = 0; l < cl; ++l)
+      for (int k = 0; k < 4; ++k)
+        for (int r = 0; r < cr; ++r) {
+          double v = A[((size_t)perm[s][l] * 4 + k) * cr + perm[s + 1][r]];
+          const int qa = q[s][perm[s][l]] / QSTRIDE + (k & 1), qb = q[s][perm[s][l]] % QSTRIDE + (k >> 1);
+          if (qa * QSTRIDE + qb != q[s + 1][perm[s + 1][r]]) v = 0.0;   // below-tolerance noise outside the blocks
+          host[base + ((size_t)l * 4 + k) * cr + r] = v;
+        }
+  }
+  // Hamiltonian in basis U and its MPO
+  std::vector<double> hU, gU;
+  rotate_integrals(c->h1.data(), c->eri.data(), U, N, hU, gU);
+  m.mpo = build_mpo(hU.data(), gU.data(), N);
+  if (m.mpo.dims[N] != 2) throw Error(TNQE_ERR_STATE, "MPO construction failed");
+  // upload
+  m.d_t = dalloc_copy(host, m.owned);
+  m.d_off = dalloc_copy(m.off, m.owned);
+  m.d_dims = dalloc_copy(m.dims, m.owned);
+  m.d_sec = dalloc_copy(m.sec, m.owned);
+  for (int t = 0; t < N; ++t) {
+    m.d_rowptr.push_back(dalloc_copy(m.mpo.sites[t].rowptr, m.owned));
+    m.d_col.push_back(dalloc_copy(m.mpo.sites[t].col, m.owned));
+    m.d_val.push_back(dalloc_copy(m.mpo.sites[t].val, m.owned));
+  }
+}
+
+}  // namespace
+
+// ============================================================================= ABI
+extern "C" {
+
+void tnqe_default_options(tnqe_options* o) {
+  if (!o) return;
+  o->precision = TNQE_PREC_FP64;
+  o->chi_rot = 0;
+  o->cutoff = 1e-14;
+  o->solve_eps = 1e-10;
+  o->renormalize_rotated = 0;
+  o->max_jacobi_sweeps = 60;
+  o->max_spin = 1LL << 26;
+  o->cuda_stream = nullptr;
+  o->device = 0;
+}
+
+tnqe_status tnqe_create(const double* h1, const double* eri, int N, int n_alpha, int n_beta,
+                        const tnqe_options* opt, tnqe_ctx** out) {
+  if (!out) return TNQE_ERR_ARG;
+  *out = nullptr;
+  tnqe_ctx* c = nullptr;
+  try {
+    if (!h1 || !eri) throw Error(TNQE_ERR_ARG, "null integrals");
+    if (N < 1 || N > 32) throw Error(TNQE_ERR_ARG, "N must be in [1, 32]");
+    if (n_alpha < 0 || n_beta < 0 || n_alpha > N || n_beta > N || n_alpha > 14 || n_beta > 14)
+      throw Error(TNQE_ERR_ARG, "electron counts must be in [0, min(N, 14)]");
+    c = new tnqe_ctx();
+    if (opt) c->opt = *opt; else tnqe_default_options(&c->opt);
+    if (c->opt.precision < 0 || c->opt.precision > 2) throw Error(TNQE_ERR_ARG, "unknown precision");
+    c->N = N;
+    c->na = n_alpha;
+    c->nb = n_beta;
+    c->h1.assign(h1, h1 + (size_t)N * N);
+    c->eri.assign(eri, eri + (size_t)N * N * N * N);
+    c->exact_dim.assign(N + 1, 0);
+    for (int b = 0; b <= N; ++b) {
+      double tot = 0.0;
+      for (int a = 0; a <= std::min(b, n_alpha); ++a)
+        for (int bb = 0; bb <= std::min(b, n_beta); ++bb) {
+          if (n_alpha - a > N - b || n_beta - bb > N - b) continue;
+          tot += std::min(binom(b, a) * binom(b, bb), binom(N - b, n_alpha - a) * binom(N - b, n_beta - bb));
+        }
+      c->exact_dim[b] = (int)std::min(tot, 1e9);
+    }
+    CK(cudaSetDevice(c->opt.device));
+    if (c->opt.cuda_stream) {
+      c->stream = (cudaStream_t)c->opt.cuda_stream;
+    } else {
+      CK(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+      c->own_stream = true;
+    }
+    for (auto& e : c->ev) CK(cudaEventCreate(&e));
+    c->pev.assign(2 + 4 * N, nullptr);
+    for (auto& e : c->pev) CK(cudaEventCreate(&e));
+    *out = c;
+    return TNQE_OK;
+  } catch (const Error& e) {
+    if (c) tnqe_destroy(c);
+    return e.st;
+  } catch (...) {
+    if (c) tnqe_destroy(c);
+    return TNQE_ERR_NOMEM;
+  }
+}
+
+tnqe_status tnqe_add_mps(tnqe_ctx* c, const double* const* tensors, const int* bond_dims, const double* U,
+                         int* mps_id) {
+  try {
+    check_ctx(c);
+    auto m = std::make_unique<DevMps>();
+    try {
+      prepare_mps(c, tensors, bond_dims, U, *m);
+    } catch (...) {
+      m->free_all();
+      throw;
+    }
+    c->mps.push_back(std::move(m));
+    if (mps_id) *mps_id = (int)c->mps.size() - 1;
+    return TNQE_OK;
+  } catch (const Error& e) {
+    return fail(c, e);
+  } catch (const std::exception& e) {
+    return fail(c, Error(TNQE_ERR_NOMEM, e.what()));
+  }
+}
+
+tnqe_status tnqe_reset_mps(tnqe_ctx* c) {
+  try {
+    check_ctx(c);
+    CK(cudaStreamSynchronize(c->stream));
+    for (auto& m : c->mps) m->free_all();
+    c->mps.clear();
+    for (auto& kv : c->plans)
+      for (void* p : kv.second->owned) cudaFree(p);
+    c->plans.clear();
+    c->kept_pair_valid = 0;
+    return TNQE_OK;
+  } catch (const Error& e) {
+    return fail(c, e);
+  }
+}
+
+tnqe_status tnqe_rotate(tnqe_ctx* c, int i, int j, double* discarded_weight) {
+  try {
+    check_ctx(c);
+    const int M = (int)c->mps.size();
+    if (i < 0 || j < 0 || i >= M || j >= M) throw Error(TNQE_ERR_STATE, "unknown MPS id");
+    c->launches = 0;
+    const int N = c->N;
+    if (i == j) {
+      c->kept_dims = c->mps[j]->dims;
+      c->kept_off = c->mps[j]->off;
+      c->kept_pair_valid = 2 + j;          // the unrotated state j
+      if (discarded_weight) *discarded_weight = 0.0;
+      return TNQE_OK;
+    }
+    RotBatch rb;
+    run_rotations(c, {{i, j}}, rb);
+    std::vector<std::vector<int>> dims;
+    std::vector<double> disc;
+    int st = 0;
+    fetch_rotation_results(c, rb, dims, disc, st);
+    c->kept_dims = dims[0];
+    c->kept_off = rb.woff[0];
+    c->kept_pair_valid = 1;
+    if (discarded_weight) *discarded_weight = disc[0];
+    (void)N;
+    if (st & STATUS_OVERFLOW) throw Error(TNQE_ERR_STATE, "rotation scratch overflow");
+    if (st & STATUS_NOCONV) throw Error(TNQE_ERR_NOCONV, "Jacobi SVD hit the sweep limit");
+    return TNQE_OK;
+  } catch (const Error& e) {
+    return fail(c, e);
+  }
+}
+
+tnqe_status tnqe_get_rotated(tnqe_ctx* c, int* bond_dims, double* tensors, long long max_doubles) {
+  try {
+    check_ctx(c);
+    if (!c->kept_pair_valid) throw Error(TNQE_ERR_STATE, "no rotated state kept");
+    const int N = c->N;
+    long long need = 0;
+    for (int s = 0; s < N; ++s) need += (long long)c->kept_dims[s] * 4 * c->kept_dims[s + 1];
+    if (bond_dims) std::memcpy(bond_dims, c->kept_dims.data(), sizeof(int) * (N + 1));
+    if (!tensors) return TNQE_OK;
+    if (max_doubles < need) throw Error(TNQE_ERR_ARG, "output buffer too small");
+    const double* base = c->kept_pair_valid == 1 ? c->rot_work.as<double>() : c->mps[c->kept_pair_valid - 2]->d_t;
+    long long o = 0;
+    for (int s = 0; s < N; ++s) {
+      const long long n = (long long)c->kept_dims[s] * 4 * c->kept_dims[s + 1];
+      CK(cudaMemcpyAsync(tensors + o, base + c->kept_off[s], sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream));
+      o += n;
+    }
+    CK(cudaStreamSynchronize(c->stream));
+    return TNQE_OK;
+  } catch (const Error& e) {
+    return fail(c, e);
+  }
+}
+
+tnqe_status tnqe_matrix_elements(tnqe_ctx* c, const int* pairs, int npairs, double* H_out, double* S_out) {
+  try {
+    check_ctx(c);
+    if (npairs < 0 || (npairs > 0 && (!pairs || !H_out || !S_out))) throw Error(TNQE_ERR_ARG, "bad pair list");
+    if (npairs == 0) return TNQE_OK;
+    const int M = (int)c->mps.size();
+    std::vector<std::pair<int, int>> pl(npairs);
+    for (int p = 0; p < npairs; ++p) {
+      const int i = pairs[2 * p], j = pairs[2 * p + 1];
+      if (i < 0 || j < 0 || i >= M || j >= M) throw Error(TNQE_ERR_STATE, "unknown MPS id in pair list");
+      if (i > j) throw Error(TNQE_ERR_ARG, "pairs must have i <= j");
+      pl[p] = {i, j};
+    }
+    if (c->opt.precision != TNQE_PREC_FP64)
+      throw Error(TNQE_ERR_ARG, "this build supports the FP64 contraction only");
+    c->launches = 0;
+    c->kept_pair_valid = 0;
+    for (double& x : c->prof) x = 0.0;
+    const int N = c->N;
+    CK(cudaEventRecord(c->ev[0], c->stream));
+    RotBatch rb;
+    run_rotations(c, pl, rb);
+    CK(cudaEventRecord(c->ev[1], c->stream));
+    std::vector<std::vector<int>> rdims;
+    std::vector<double> disc;
+    int st = 0;
+    fetch_rotation_results(c, rb, rdims, disc, st);
+    if (st & STATUS_OVERFLOW) throw Error(TNQE_ERR_STATE, "rotation scratch overflow");
+    std::vector<KetView> kets(npairs);
+    for (int p = 0; p < npairs; ++p) {
+      const DevMps& mi = *c->mps[pl[p].first];
+      kets[p].base = mi.d_t;
+      kets[p].off = mi.off;
+      kets[p].dims = mi.dims;
+    }
+    for (size_t k = 0; k < rb.pair_idx.size(); ++k) {
+      KetView& kv = kets[rb.pair_idx[k]];
+      kv.base = rb.work[k];
+      kv.off = rb.woff[k];
+      kv.dims = rdims[k];
+    }
+    CK(cudaEventRecord(c->ev[2], c->stream));
+    c->con_out.ensure(sizeof(double) * 2 * npairs);
+    double* dH = c->con_out.as<double>();
+    double* dS = dH + npairs;
+    run_contractions(c, pl, kets, dH, dS);
+    CK(cudaEventRecord(c->ev[3], c->stream));
+    const bool hdev = is_device_ptr(H_out), sdev = is_device_ptr(S_out);
+    CK(cudaMemcpyAsync(H_out, dH, sizeof(double) * npairs, hdev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                       c->stream));
+    CK(cudaMemcpyAsync(S_out, dS, sizeof(double) * npairs, sdev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                       c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    float t01 = 0, t23 = 0, t03 = 0;
+    CK(cudaEventElapsedTime(&t01, c->ev[0], c->ev[1]));
+    CK(cudaEventElapsedTime(&t23, c->ev[2], c->ev[3]));
+    CK(cudaEventElapsedTime(&t03, c->ev[0], c->ev[3]));
+    c->times[0] = t01;
+    c->times[1] = t23;
+    c->times[2] = t03;
+    (void)N;
+    if (st & STATUS_NOCONV)
+      throw Error(TNQE_ERR_NOCONV, "Jacobi SVD hit the sweep limit on a " + std::to_string((st >> 8) & 4095) + " x " +
+                                       std::to_string((st >> 20) & 4095) + " block (results written)");
+    return TNQE_OK;
+  } catch (const Error& e) {
+    return fail(c, e);
+  } catch (const std::exception& e) {
+    return fail(c, Error(TNQE_ERR_NOMEM, e.what()));
+  }
+}
+
+tnqe_status tnqe_solve(tnqe_ctx* c, const double* H, const double* S, int M, double* E, double* C, int* rank_kept,
+                       double* kappa1) {
+  try {
+    check_ctx(c);
+    if (M < 1 || M > 32 || !H || !S || !E || !C || !rank_kept || !kappa1) throw Error(TNQE_ERR_ARG, "bad solve arguments");
+    DBuf buf;
+    const size_t mm = (size_t)M * M;
+    buf.ensure(sizeof(double) * (3 * mm + M + 2) + 16);
+    double* dH = buf.as<double>();
+    double* dS = dH + mm;
+    double* dC = dS + mm;
+    double* dE = dC + mm;
+    double* dK = dE + M;
+    int* dR = reinterpret_cast<int*>(dK + 1);
+    int* dSt = dR + 1;
+    CK(cudaMemcpyAsync(dH, H, sizeof(double) * mm, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(dS, S, sizeof(double) * mm, cudaMemcpyHostToDevice, c->stream));
+    CKL(launch_solve(dH, dS, M, c->opt.solve_eps, c->opt.max_jacobi_sweeps, dE, dC, dR, dK, dSt, c->stream));
+    int st = 0;
+    CK(cudaMemcpyAsync(E, dE, sizeof(double) * M, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(C, dC, sizeof(double) * mm, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(rank_kept, dR, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(kappa1, dK, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(&st, dSt, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    buf.release();
+    if (st) throw Error(TNQE_ERR_NOCONV, "eigensolver hit the sweep limit");
+    return TNQE_OK;
+  } catch (const Error& e) {
+    return fail(c, e);
+  }
+}
+
+tnqe_status tnqe_set_precision(tnqe_ctx* c, int precision) {
+  if (!c) return TNQE_ERR_ARG;
+  if (precision < 0 || precision > 2) {
+    c->err = "unknown precision";
+    return TNQE_ERR_ARG;
+  }
+  c->opt.precision = precision;
+  return TNQE_OK;
+}
+
+tnqe_status tnqe_last_timing(const tnqe_ctx* c, double* times, int* launches) {
+  if (!c) return TNQE_ERR_ARG;
+  if (times)
+    for (int k = 0; k < 3; ++k) times[k] = c->times[k];
+  if (launches) *launches = c->launches;
+  return TNQE_OK;
+}
+
+tnqe_status tnqe_last_profile(const tnqe_ctx* c, double* prof, int n) {
+  if (!c || !prof || n < 0) return TNQE_ERR_ARG;
+  for (int k = 0; k < n && k < 10; ++k) prof[k] = c->prof[k];
+  if (n > 9) prof[9] = c->launches;
+  return TNQE_OK;
+}
+
+const char* tnqe_last_error(const tnqe_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+void tnqe_destroy(tnqe_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->opt.device);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  for (auto& m : c->mps) m->free_all();
+  for (auto& kv : c->plans)
+    for (void* p : kv.second->owned) cudaFree(p);
+  c->rot_work.release();
+  c->rot_scratch.release();
+  c->rot_meta.release();
+  c->rot_small.release();
+  c->rot_desc.release();
+  c->con_ws.release();
+  c->con_desc.release();
+  c->con_out.release();
+  for (auto& e : c->ev)
+    if (e) cudaEventDestroy(e);
+  for (auto& e : c->pev)
+    if (e) cudaEventDestroy(e);
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,114 @@
+// Internal declarations shared by the host planner, the kernels and the ABI layer.
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#ifdef __CUDACC__
+#define TNQE_HD __host__ __device__
+#else
+#define TNQE_HD
+#endif
+
+namespace tnqe {
+
+// A particle-number charge (n_alpha, n_beta) is coded as n_alpha * 16 + n_beta.
+constexpr int QSTRIDE = 16;
+constexpr int QSPACE = 256;
+constexpr int MAXSEC = 160;            // sectors per bond
+TNQE_HD inline int local_charge(int k) { return (k & 1) * QSTRIDE + (k >> 1); }
+
+struct SectorTable {                   // one bond: sectors in ascending charge
+  int nsec;
+  int q[MAXSEC];
+  int off[MAXSEC];
+  int dim[MAXSEC];
+};
+
+// ----------------------------------------------------------------------------- host planning
+struct Gate {
+  int site;        // acts on sites (site, site+1)
+  int side;        // 0: singular values join the left tensor, 1: the right tensor
+  double c, s;     // rotation J = [[c, -s], [s, c]] at rows/columns (site, site+1)
+};
+
+struct GivensPlan {
+  std::vector<Gate> gates;   // in application order
+  int neg_site;              // site whose orbital flips sign (det V = -1), else -1
+};
+
+GivensPlan givens_plan(const double* V, int N);
+void gate_matrix(double c, double s, double* G16x16);   // row (k1',k2'), col (k1,k2), K = 4 k1 + k2
+void rotate_integrals(const double* h1, const double* eri, const double* U, int N,
+                      std::vector<double>& h_out, std::vector<double>& eri_out);
+
+struct MpoSite {            // stage-2 operator of one site as CSR over output rows
+  int Din, Dout;            // channels at bond t and t+1
+  std::vector<int> rowptr;  // size 4*Dout + 1, row = k * Dout + w'
+  std::vector<int> col;     // w * 4 + k'
+  std::vector<double> val;
+};
+struct Mpo {
+  std::vector<int> dims;    // N + 1 channel counts; channel 0 = identity string, 1 = completed H
+  std::vector<MpoSite> sites;
+};
+Mpo build_mpo(const double* h1, const double* eri, int N);
+
+// ----------------------------------------------------------------------------- device descriptors
+struct RotDesc {
+  int N, chi_rot, ngates, neg_site, renorm, max_sweeps;
+  double cutoff;
+  const double* src;              // input MPS j
+  const long long* src_off;       // N site offsets into src
+  const int* src_dims;            // N + 1
+  const SectorTable* src_sec;     // N + 1
+  double* work;                   // rotated MPS, per-site capacity
+  const long long* work_off;      // N site offsets into work
+  int* work_dims;                 // N + 1
+  const int* work_cap;            // N + 1 bond capacities
+  SectorTable* work_sec;          // N + 1
+  const double* gates;            // ngates * 256
+  const int* gate_site;
+  const int* gate_side;
+  double* theta;                  // scratch
+  double* wbuf;
+  double* qbuf;
+  int* meta;                      // scratch ints
+  long long meta_cap;
+  double* discarded;
+  int* status;
+  double* flops;                  // algorithmic FLOPs of this rotation (written at exit)
+};
+
+struct GemmDesc {                 // C[M x N] = op(A) * B ; all row-major
+  int M, N, K, transA;            // transA: A stored K x M
+  int lda, ldb, ldc, pad;
+  const double* A;
+  const double* B;
+  double* C;
+};
+
+struct SpmmDesc {                 // Y[a][row][:] = sum val * X[a][col][:], rows = 4*Dout (k*Dout + w')
+  int chi_a, nrows, ncols_x, width;  // width = ket bond dim (b')
+  const int* rowptr;
+  const int* col;
+  const double* val;
+  const double* X;                // [a][4*Din][width]
+  double* Y;                      // [a][4][Dout][width] == [a][nrows][width]
+};
+
+// status bits written by kernels
+constexpr int STATUS_NOCONV = 1;
+constexpr int STATUS_OVERFLOW = 2;
+
+// kernel launchers (kernels_*.cu); return cudaError_t as int
+int launch_rotate(const RotDesc* d_descs, int npairs, int smem_bytes, void* stream);
+int launch_gemm_f64(const GemmDesc* d_descs, const long long* d_tile_prefix, int nprob,
+                    long long total_tiles, void* stream);
+int launch_spmm_f64(const SpmmDesc* d_descs, const long long* d_row_prefix, int nprob,
+                    long long total_rows, void* stream);
+int launch_extract(const double* const* d_final, int npairs, double* H, double* S, void* stream);
+int launch_solve(const double* d_H, const double* d_S, int M, double eps, int max_sweeps,
+                 double* d_E, double* d_C, int* d_rank, double* d_kappa, int* d_status, void* stream);
+
+}  // namespace tnqe

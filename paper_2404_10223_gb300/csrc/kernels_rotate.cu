@@ -1,0 +1,498 @@
+// Rotation of MPS j into the orbital basis of MPS i (Eq. 11, Sec. II D, App. A3):
+// one CTA per pair walks that pair's Givens gates in order.  Per gate on sites
+// (a, a+1): contract the two-site tensor, apply the 16 x 16 gate, split the
+// result into particle-number blocks of the new middle bond, take an FP64
+// one-sided Jacobi SVD of every block, keep the largest singular values
+// globally (k <= chi_rot, sigma > cutoff * sigma_1) and write the two new site
+// tensors.  The tensors stay dense in memory; only their charge-allowed blocks
+// are computed, since a Givens gate conserves (n_alpha, n_beta) per spin.
+#include <cuda_runtime.h>
+
+#include "internal.h"
+
+namespace tnqe {
+namespace {
+
+constexpr int ROT_THREADS = 256;
+constexpr int ROT_WARPS = ROT_THREADS / 32;
+constexpr int MAXSIG = 1024;       // singular values of one gate: <= 4 * min(chi_l, chi_r)
+
+struct ThetaBlk {                  // one (left sector, k1, k2) block of the two-site tensor
+  int sL, sM, sR, k1, k2, start;
+};
+struct NewBlk {                    // one charge block of the new middle bond
+  int q, nr, nc;
+  int rowsec[4], rowoff[4];        // per k1': left sector (-1 none) and row offset in block
+  int colsec[4], coloff[4];        // per k2': right sector and column offset
+  long long wofs, qofs;            // offsets in wbuf / qbuf
+  int sofs;                        // first singular value in the gate's list
+  int kept, newoff;
+  double scale;                    // the block is stored divided by its largest |entry|
+};
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ int qsub(int q, int qk) {      // q - qk, -1 if a component goes negative
+  int qa = q / QSTRIDE - qk / QSTRIDE, qb = q % QSTRIDE - qk % QSTRIDE;
+  return (qa < 0 || qb < 0) ? -1 : qa * QSTRIDE + qb;
+}
+__device__ __forceinline__ int qadd(int q, int qk) {
+  int qa = q / QSTRIDE + qk / QSTRIDE, qb = q % QSTRIDE + qk % QSTRIDE;
+  return (qa >= QSTRIDE || qb >= QSTRIDE) ? -1 : qa * QSTRIDE + qb;
+}
+
+// pair (i, j) of round r of the circle-method tournament over n2 (even) columns
+__device__ __forceinline__ void tour_pair(int r, int k, int n2, int& i, int& j) {
+  const int m = n2 - 1;
+  if (k == 0) {
+    i = r;
+    j = m;
+  } else {
+    i = (r + k) % m;
+    j = (r - k + m) % m;
+  }
+}
+
+// One-sided Jacobi on W (m x n, column-major, n <= m) accumulating Q (n x n).
+// Columns become mutually orthogonal: W_final = W_0 Q.  Returns 1 if it hit the
+// sweep limit.
+__device__ int jacobi_block(double* W, double* Q, int m, int n, int max_sweeps, int* flag) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int idx = tid; idx < n * n; idx += ROT_THREADS) Q[idx] = ((idx / n) == (idx % n)) ? 1.0 : 0.0;
+  __syncthreads();
+  if (n < 2) return 0;
+  const double tol = 2.220446049250313e-16 * (double)m;
+  const int n2 = n + (n & 1);
+  int noconv = 1;
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    if (tid == 0) *flag = 0;
+    __syncthreads();
+    for (int r = 0; r < n2 - 1; ++r) {
+      for (int k = warp; k < n2 / 2; k += ROT_WARPS) {
+        int i, j;
+        tour_pair(r, k, n2, i, j);
+        if (i >= n || j >= n) continue;
+        double* x = W + (size_t)i * m;
+        double* y = W + (size_t)j * m;
+        double al = 0.0, be = 0.0, ga = 0.0;
+        for (int t = lane; t < m; t += 32) {
+          const double xv = x[t], yv = y[t];
+          al = fma(xv, xv, al);
+          be = fma(yv, yv, be);
+          ga = fma(xv, yv, ga);
+        }
+        al = warp_sum(al);
+        be = warp_sum(be);
+        ga = warp_sum(ga);
+        // columns below 1e-125 of the block's largest entry are zero at this precision
+        if (ga == 0.0 || al < 1e-250 || be < 1e-250 || !(fabs(ga) > tol * sqrt(al) * sqrt(be))) continue;
+        const double zeta = (be - al) / (2.0 * ga);
+        const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + hypot(1.0, zeta));
+        const double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
+        if (s == 0.0) continue;                      // rotation below resolution: nothing changes
+        for (int u = lane; u < m; u += 32) {
+          const double xv = x[u], yv = y[u];
+          x[u] = c * xv - s * yv;
+          y[u] = s * xv + c * yv;
+        }
+        double* qx = Q + (size_t)i * n;
+        double* qy = Q + (size_t)j * n;
+        for (int u = lane; u < n; u += 32) {
+          const double xv = qx[u], yv = qy[u];
+          qx[u] = c * xv - s * yv;
+          qy[u] = s * xv + c * yv;
+        }
+        if (lane == 0) *flag = 1;
+      }
+      __syncthreads();
+    }
+    const int any = *flag;
+    __syncthreads();
+    if (!any) {
+      noconv = 0;
+      break;
+    }
+  }
+  return noconv;
+}
+
+__global__ void __launch_bounds__(ROT_THREADS) rotate_pairs_kernel(const RotDesc* __restrict__ descs) {
+  const RotDesc& D = descs[blockIdx.x];
+  const int tid = threadIdx.x;
+  const int N = D.N;
+
+  __shared__ int lutL[QSPACE], lutM[QSPACE], lutR[QSPACE];
+  __shared__ SectorTable secL, secM, secR;
+  __shared__ double G[256];
+  __shared__ int gnz_n[16], gnz_k[16][16];
+  __shared__ double gnz_v[16][16];
+  __shared__ double sig[MAXSIG];
+  __shared__ short sig_blk[MAXSIG], sig_col[MAXSIG];
+  __shared__ unsigned char sig_keep[MAXSIG];
+  __shared__ int s_nblk, s_nnew, s_total, s_nsig, s_keep, s_flag, s_status;
+  __shared__ double s_disc, s_smax, s_red[ROT_WARPS], s_flops;
+
+  ThetaBlk* tb = reinterpret_cast<ThetaBlk*>(D.meta);
+  const long long tb_cap = D.meta_cap / 2 / (long long)(sizeof(ThetaBlk) / sizeof(int));
+  NewBlk* nb = reinterpret_cast<NewBlk*>(D.meta + D.meta_cap / 2);
+  const long long nb_cap = D.meta_cap / 2 / (long long)(sizeof(NewBlk) / sizeof(int));
+
+  // ---- copy the input state into the work buffer
+  for (int s = 0; s < N; ++s) {
+    const long long n = (long long)D.src_dims[s] * 4 * D.src_dims[s + 1];
+    const double* src = D.src + D.src_off[s];
+    double* dst = D.work + D.work_off[s];
+    for (long long x = tid; x < n; x += ROT_THREADS) dst[x] = src[x];
+  }
+  for (int b = tid; b <= N; b += ROT_THREADS) {
+    D.work_dims[b] = D.src_dims[b];
+    D.work_sec[b] = D.src_sec[b];
+  }
+  if (tid == 0) {
+    s_disc = 0.0;
+    s_status = 0;
+    s_flops = 0.0;
+  }
+  __syncthreads();
+
+  for (int g = 0; g < D.ngates; ++g) {
+    const int a = D.gate_site[g];
+    const int side = D.gate_side[g];
+    for (int x = tid; x < QSPACE; x += ROT_THREADS) {
+      lutL[x] = -1;
+      lutM[x] = -1;
+      lutR[x] = -1;
+    }
+    if (tid == 0) {
+      secL = D.work_sec[a];
+      secM = D.work_sec[a + 1];
+      secR = D.work_sec[a + 2];
+    }
+    for (int x = tid; x < 256; x += ROT_THREADS) G[x] = D.gates[(size_t)g * 256 + x];
+    __syncthreads();
+    for (int x = tid; x < secL.nsec; x += ROT_THREADS) lutL[secL.q[x]] = x;
+    for (int x = tid; x < secM.nsec; x += ROT_THREADS) lutM[secM.q[x]] = x;
+    for (int x = tid; x < secR.nsec; x += ROT_THREADS) lutR[secR.q[x]] = x;
+    if (tid < 16) {                       // nonzero inputs of each gate row
+      int c = 0;
+      for (int K = 0; K < 16; ++K) {
+        const double v = G[tid * 16 + K];
+        if (v != 0.0) {
+          gnz_k[tid][c] = K;
+          gnz_v[tid][c] = v;
+          ++c;
+        }
+      }
+      gnz_n[tid] = c;
+    }
+    const int chl = D.work_dims[a], chm = D.work_dims[a + 1], chr = D.work_dims[a + 2];
+    double* Lt = D.work + D.work_off[a];
+    double* Rt = D.work + D.work_off[a + 1];
+    __syncthreads();
+
+    // ---- two-site tensor theta[l][k1][k2][r], charge-allowed blocks only
+    if (tid == 0) {
+      int nblk = 0, start = 0;
+      for (int sL = 0; sL < secL.nsec; ++sL)
+        for (int k1 = 0; k1 < 4; ++k1) {
+          const int qM = qadd(secL.q[sL], local_charge(k1));
+          const int sM = qM < 0 ? -1 : lutM[qM];
+          if (sM < 0) continue;
+          for (int k2 = 0; k2 < 4; ++k2) {
+            const int qR = qadd(qM, local_charge(k2));
+            const int sR = qR < 0 ? -1 : lutR[qR];
+            if (sR < 0) continue;
+            if (nblk < tb_cap) tb[nblk] = ThetaBlk{sL, sM, sR, k1, k2, start};
+            ++nblk;
+            start += secL.dim[sL] * secR.dim[sR];
+            s_flops += 2.0 * secL.dim[sL] * secM.dim[sM] * secR.dim[sR];
+          }
+        }
+      if (nblk > tb_cap) {
+        s_status |= STATUS_OVERFLOW;
+        nblk = (int)tb_cap;
+      }
+      s_nblk = nblk;
+      s_total = start;
+    }
+    __syncthreads();
+    {
+      const int nblk = s_nblk, total = s_total;
+      for (int idx = tid; idx < total; idx += ROT_THREADS) {
+        int lo = 0, hi = nblk - 1;
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (tb[mid].start <= idx) lo = mid; else hi = mid - 1;
+        }
+        const ThetaBlk B = tb[lo];
+        const int dR = secR.dim[B.sR];
+        const int li = (idx - B.start) / dR, ri = (idx - B.start) % dR;
+        const int l = secL.off[B.sL] + li, r = secR.off[B.sR] + ri;
+        const int m0 = secM.off[B.sM], m1 = m0 + secM.dim[B.sM];
+        const double* lrow = Lt + ((size_t)l * 4 + B.k1) * chm;
+        const double* rcol = Rt + (size_t)B.k2 * chr + r;
+        double acc = 0.0;
+        for (int m = m0; m < m1; ++m) acc = fma(lrow[m], rcol[(size_t)m * 4 * chr], acc);
+        D.theta[(((size_t)l * 4 + B.k1) * 4 + B.k2) * chr + r] = acc;
+      }
+    }
+    // ---- blocks of the new middle bond, ascending charge
+    if (tid == 0) {
+      int nnew = 0, nsig = 0;
+      long long wofs = 0, qofs = 0;
+      for (int q = 0; q < QSPACE; ++q) {
+        NewBlk B;
+        B.q = q;
+        int nr = 0, nc = 0;
+        for (int k = 0; k < 4; ++k) {
+          const int qL = qsub(q, local_charge(k));
+          const int sL = qL < 0 ? -1 : lutL[qL];
+          B.rowsec[k] = sL;
+          B.rowoff[k] = nr;
+          if (sL >= 0) nr += secL.dim[sL];
+          const int qR = qadd(q, local_charge(k));
+          const int sR = qR < 0 ? -1 : lutR[qR];
+          B.colsec[k] = sR;
+          B.coloff[k] = nc;
+          if (sR >= 0) nc += secR.dim[sR];
+        }
+        if (nr == 0 || nc == 0) continue;
+        B.nr = nr;
+        B.nc = nc;
+        const int mm = nr > nc ? nr : nc, nn = nr > nc ? nc : nr;
+        B.wofs = wofs;
+        B.qofs = qofs;
+        B.sofs = nsig;
+        B.kept = 0;
+        B.newoff = 0;
+        wofs += (long long)mm * nn;
+        qofs += (long long)nn * nn;
+        s_flops += 4.0 * mm * nn * nn + 8.0 * nn * nn * nn + 8.0 * mm * nn;
+        nsig += nn;
+        if (nnew < nb_cap && nsig <= MAXSIG) nb[nnew] = B;
+        ++nnew;
+      }
+      if (nnew > nb_cap || nsig > MAXSIG) {
+        s_status |= STATUS_OVERFLOW;
+        nnew = 0;
+        nsig = 0;
+      }
+      s_nnew = nnew;
+      s_nsig = nsig;
+    }
+    __syncthreads();
+    const int nnew = s_nnew;
+    // ---- SVD of every block
+    for (int b = 0; b < nnew; ++b) {
+      const NewBlk B = nb[b];
+      const bool trans = B.nc > B.nr;                // work on B^T so that n <= m
+      const int m = trans ? B.nc : B.nr, n = trans ? B.nr : B.nc;
+      double* W = D.wbuf + B.wofs;
+      double* Q = D.qbuf + B.qofs;
+      for (int idx = tid; idx < m * n; idx += ROT_THREADS) {
+        const int wi = idx % m, wj = idx / m;
+        const int br = trans ? wj : wi, bc = trans ? wi : wj;
+        int k1p = 3, k2p = 3;
+        while (k1p > 0 && (B.rowsec[k1p] < 0 || B.rowoff[k1p] > br)) --k1p;
+        while (k2p > 0 && (B.colsec[k2p] < 0 || B.coloff[k2p] > bc)) --k2p;
+        const int sL = B.rowsec[k1p], sR = B.colsec[k2p];
+        const int l = secL.off[sL] + (br - B.rowoff[k1p]);
+        const int r = secR.off[sR] + (bc - B.coloff[k2p]);
+        const int Kp = k1p * 4 + k2p;
+        double acc = 0.0;
+        for (int e = 0; e < gnz_n[Kp]; ++e) {
+          const int K = gnz_k[Kp][e];
+          const int k1 = K >> 2, k2 = K & 3;
+          const int qM = qadd(secL.q[sL], local_charge(k1));
+          if (qM < 0 || lutM[qM] < 0) continue;       // that theta block is zero
+          acc = fma(gnz_v[Kp][e], D.theta[(((size_t)l * 4 + k1) * 4 + k2) * chr + r], acc);
+        }
+        W[idx] = acc;
+      }
+      __syncthreads();
+      {
+        double mx = 0.0;
+        for (int idx = tid; idx < m * n; idx += ROT_THREADS) mx = fmax(mx, fabs(W[idx]));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if ((tid & 31) == 0) s_red[tid >> 5] = mx;
+        __syncthreads();
+        double bmax = 0.0;
+        for (int w = 0; w < ROT_WARPS; ++w) bmax = fmax(bmax, s_red[w]);
+        const double scale = bmax > 0.0 ? bmax : 1.0;
+        const double inv = 1.0 / scale;
+        for (int idx = tid; idx < m * n; idx += ROT_THREADS) W[idx] *= inv;
+        if (tid == 0) nb[b].scale = scale;
+        __syncthreads();
+      }
+      const int nc_flag = jacobi_block(W, Q, m, n, D.max_sweeps, &s_flag);
+      if (nc_flag && tid == 0) s_status |= STATUS_NOCONV | (min(m, 4095) << 8) | (min(n, 4095) << 20);
+      // singular values = column norms
+      for (int j = 0; j < n; ++j) {
+        double acc = 0.0;
+        for (int u = tid; u < m; u += ROT_THREADS) {
+          const double v = W[(size_t)j * m + u];
+          acc = fma(v, v, acc);
+        }
+        acc = warp_sum(acc);
+        if ((tid & 31) == 0) s_red[tid >> 5] = acc;
+        __syncthreads();
+        if (tid == 0) {
+          double t = 0.0;
+          for (int w = 0; w < ROT_WARPS; ++w) t += s_red[w];
+          sig[B.sofs + j] = sqrt(t) * nb[b].scale;
+          sig_blk[B.sofs + j] = (short)b;
+          sig_col[B.sofs + j] = (short)j;
+        }
+        __syncthreads();
+      }
+    }
+    // ---- global truncation: k = min(chi_rot, #{sigma > cutoff sigma_1}), at least 1
+    const int nsig = s_nsig;
+    if (tid == 0) {
+      double smax = 0.0;
+      for (int x = 0; x < nsig; ++x) smax = fmax(smax, sig[x]);
+      int above = 0;
+      for (int x = 0; x < nsig; ++x) above += (sig[x] > D.cutoff * smax) ? 1 : 0;
+      int keep = above < D.chi_rot ? above : D.chi_rot;
+      if (keep > D.work_cap[a + 1]) keep = D.work_cap[a + 1];
+      if (keep < 1) keep = 1;
+      if (keep > nsig) keep = nsig;
+      s_keep = keep;
+      s_smax = smax;
+    }
+    __syncthreads();
+    for (int x = tid; x < nsig; x += ROT_THREADS) {
+      const double v = sig[x];
+      int rank = 0;
+      for (int y = 0; y < nsig; ++y) rank += (sig[y] > v || (sig[y] == v && y < x)) ? 1 : 0;
+      sig_keep[x] = rank < s_keep ? 1 : 0;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      double disc = 0.0;
+      for (int x = 0; x < nsig; ++x)
+        if (!sig_keep[x]) disc += sig[x] * sig[x];
+      s_disc += disc;
+      int off = 0;
+      SectorTable& nt = secM;                       // reuse as the new middle table
+      nt.nsec = 0;
+      for (int b = 0; b < nnew; ++b) {
+        int kept = 0;
+        for (int j = 0; j < (nb[b].nr < nb[b].nc ? nb[b].nr : nb[b].nc); ++j) kept += sig_keep[nb[b].sofs + j];
+        nb[b].kept = kept;
+        nb[b].newoff = off;
+        if (kept > 0) {
+          nt.q[nt.nsec] = nb[b].q;
+          nt.off[nt.nsec] = off;
+          nt.dim[nt.nsec] = kept;
+          ++nt.nsec;
+        }
+        off += kept;
+      }
+      D.work_sec[a + 1] = nt;
+      D.work_dims[a + 1] = off;
+    }
+    __syncthreads();
+    // ---- write the two new site tensors
+    const int knew = D.work_dims[a + 1];
+    for (long long x = tid; x < (long long)chl * 4 * knew; x += ROT_THREADS) Lt[x] = 0.0;
+    for (long long x = tid; x < (long long)knew * 4 * chr; x += ROT_THREADS) Rt[x] = 0.0;
+    __syncthreads();
+    for (int b = 0; b < nnew; ++b) {
+      const NewBlk B = nb[b];
+      if (B.kept == 0) continue;
+      const bool trans = B.nc > B.nr;
+      const int m = trans ? B.nc : B.nr, n = trans ? B.nr : B.nc;
+      const double* W = D.wbuf + B.wofs;
+      const double* Q = D.qbuf + B.qofs;
+      const double bs = B.scale;
+      int newidx = B.newoff;
+      for (int j = 0; j < n; ++j) {
+        if (!sig_keep[B.sofs + j]) continue;
+        const double sj = sig[B.sofs + j];
+        const double inv = sj > 0.0 ? 1.0 / sj : 0.0;
+        // left factor column over block rows (l, k1'), right factor row over block cols (k2', r)
+        for (int br = tid; br < B.nr; br += ROT_THREADS) {
+          int k1p = 3;
+          while (k1p > 0 && (B.rowsec[k1p] < 0 || B.rowoff[k1p] > br)) --k1p;
+          const int l = secL.off[B.rowsec[k1p]] + (br - B.rowoff[k1p]);
+          double v;
+          if (!trans) v = (side == 0) ? W[(size_t)j * m + br] * bs : W[(size_t)j * m + br] * bs * inv;
+          else v = (side == 0) ? Q[(size_t)j * n + br] * sj : Q[(size_t)j * n + br];
+          Lt[((size_t)l * 4 + k1p) * knew + newidx] = v;
+        }
+        for (int bc = tid; bc < B.nc; bc += ROT_THREADS) {
+          int k2p = 3;
+          while (k2p > 0 && (B.colsec[k2p] < 0 || B.coloff[k2p] > bc)) --k2p;
+          const int r = secR.off[B.colsec[k2p]] + (bc - B.coloff[k2p]);
+          double v;
+          if (!trans) v = (side == 0) ? Q[(size_t)j * n + bc] : Q[(size_t)j * n + bc] * sj;
+          else v = (side == 0) ? W[(size_t)j * m + bc] * bs * inv : W[(size_t)j * m + bc] * bs;
+          Rt[((size_t)newidx * 4 + k2p) * chr + r] = v;
+        }
+        ++newidx;
+      }
+    }
+    __syncthreads();
+  }
+
+  // ---- G(D): the orbital of a -1 diagonal entry flips both spins' creators
+  if (D.neg_site >= 0) {
+    const int s = D.neg_site;
+    double* T = D.work + D.work_off[s];
+    const int cl = D.work_dims[s], cr = D.work_dims[s + 1];
+    for (long long x = tid; x < (long long)cl * 4 * cr; x += ROT_THREADS) {
+      const int k = (int)((x / cr) % 4);
+      if (k == 1 || k == 2) T[x] = -T[x];
+    }
+    __syncthreads();
+  }
+  // ---- optional renormalisation to the input norm (the centre holds the norm)
+  if (D.renorm && D.ngates > 0) {
+    const int lastg = D.ngates - 1;
+    const int c = D.gate_site[lastg] + (D.gate_side[lastg] ? 1 : 0);
+    double* T = D.work + D.work_off[c];
+    const long long n = (long long)D.work_dims[c] * 4 * D.work_dims[c + 1];
+    const double* S0 = D.src + D.src_off[N - 1];
+    const long long n0 = (long long)D.src_dims[N - 1] * 4;
+    double a1 = 0.0, a0 = 0.0;
+    for (long long x = tid; x < n; x += ROT_THREADS) a1 = fma(T[x], T[x], a1);
+    for (long long x = tid; x < n0; x += ROT_THREADS) a0 = fma(S0[x], S0[x], a0);
+    a1 = warp_sum(a1);
+    a0 = warp_sum(a0);
+    __shared__ double r1[ROT_WARPS], r0[ROT_WARPS];
+    if ((tid & 31) == 0) {
+      r1[tid >> 5] = a1;
+      r0[tid >> 5] = a0;
+    }
+    __syncthreads();
+    double t1 = 0.0, t0 = 0.0;
+    for (int w = 0; w < ROT_WARPS; ++w) {
+      t1 += r1[w];
+      t0 += r0[w];
+    }
+    const double f = t1 > 0.0 ? sqrt(t0 / t1) : 1.0;
+    for (long long x = tid; x < n; x += ROT_THREADS) T[x] *= f;
+  }
+  if (tid == 0) {
+    *D.discarded = s_disc;
+    *D.status = s_status;
+    *D.flops = s_flops;
+  }
+}
+
+}  // namespace
+
+int launch_rotate(const RotDesc* d_descs, int npairs, int smem_bytes, void* stream) {
+  if (npairs <= 0) return 0;
+  (void)smem_bytes;
+  rotate_pairs_kernel<<<npairs, ROT_THREADS, 0, (cudaStream_t)stream>>>(d_descs);
+  return (int)cudaGetLastError();
+}
+
+}  // namespace tnqe

@@ -1,0 +1,242 @@
+"""Thin ctypes binding of the C ABI in ``include/tnqe.h`` (argument marshalling only).
+
+Every function here has the name of the C entry point it calls and does no
+arithmetic of the method: arrays are made contiguous FP64 and passed as
+pointers; device buffers (for example ``torch.Tensor.data_ptr()``) may be
+passed as plain integers wherever the ABI accepts host or device memory.
+The library must have been built (``build.py``); loading fails loudly
+otherwise -- there is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import List, Optional, Sequence, Tuple
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libtnqe.so")
+
+TNQE_PREC_FP64, TNQE_PREC_TF32X3, TNQE_PREC_BF16X3 = 0, 1, 2
+STATUS_NAMES = {0: "TNQE_OK", 1: "TNQE_ERR_ARG", 2: "TNQE_ERR_STATE", 3: "TNQE_ERR_NOMEM", 4: "TNQE_ERR_CUDA",
+                5: "TNQE_ERR_NOCONV", 6: "TNQE_ERR_TIMEOUT", 7: "TNQE_ERR_NUMERIC"}
+
+
+class TnqeError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class tnqe_options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("chi_rot", ctypes.c_int), ("cutoff", ctypes.c_double),
+                ("solve_eps", ctypes.c_double), ("renormalize_rotated", ctypes.c_int),
+                ("max_jacobi_sweeps", ctypes.c_int), ("max_spin", ctypes.c_longlong),
+                ("cuda_stream", ctypes.c_void_p), ("device", ctypes.c_int)]
+
+
+EXPORTED = ["tnqe_default_options", "tnqe_create", "tnqe_add_mps", "tnqe_reset_mps", "tnqe_rotate",
+            "tnqe_get_rotated", "tnqe_matrix_elements", "tnqe_solve", "tnqe_set_precision", "tnqe_last_timing", "tnqe_last_profile",
+            "tnqe_last_error", "tnqe_destroy"]
+
+_lib = None
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libtnqe.so not built at {path}; run paper_2404_10223_gb300/build.py")
+    lib = ctypes.CDLL(path)
+    P, I, D, LL = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_longlong
+    lib.tnqe_default_options.argtypes = [ctypes.POINTER(tnqe_options)]
+    lib.tnqe_default_options.restype = None
+    lib.tnqe_create.argtypes = [P, P, I, I, I, ctypes.POINTER(tnqe_options), ctypes.POINTER(P)]
+    lib.tnqe_add_mps.argtypes = [P, P, P, P, ctypes.POINTER(I)]
+    lib.tnqe_reset_mps.argtypes = [P]
+    lib.tnqe_rotate.argtypes = [P, I, I, ctypes.POINTER(D)]
+    lib.tnqe_get_rotated.argtypes = [P, P, P, LL]
+    lib.tnqe_matrix_elements.argtypes = [P, P, I, P, P]
+    lib.tnqe_solve.argtypes = [P, P, P, I, P, P, ctypes.POINTER(I), ctypes.POINTER(D)]
+    lib.tnqe_set_precision.argtypes = [P, I]
+    lib.tnqe_last_timing.argtypes = [P, P, ctypes.POINTER(I)]
+    lib.tnqe_last_profile.argtypes = [P, P, I]
+    lib.tnqe_last_error.argtypes = [P]
+    lib.tnqe_last_error.restype = ctypes.c_char_p
+    lib.tnqe_destroy.argtypes = [P]
+    lib.tnqe_destroy.restype = None
+    for name in EXPORTED:
+        if name not in ("tnqe_default_options", "tnqe_last_error", "tnqe_destroy"):
+            getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _ptr(a):
+    if isinstance(a, int):
+        return ctypes.c_void_p(a)
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _check(ctx, st: int):
+    if st != 0:
+        msg = load().tnqe_last_error(ctx).decode() if ctx else ""
+        raise TnqeError(st, msg)
+
+
+def tnqe_default_options() -> tnqe_options:
+    o = tnqe_options()
+    load().tnqe_default_options(ctypes.byref(o))
+    return o
+
+
+def tnqe_create(h1, eri, N: int, n_alpha: int, n_beta: int, options: Optional[tnqe_options] = None):
+    lib = load()
+    h1, eri = _f64(h1), _f64(eri)
+    out = ctypes.c_void_p()
+    st = lib.tnqe_create(_ptr(h1), _ptr(eri), N, n_alpha, n_beta,
+                         ctypes.byref(options) if options is not None else None, ctypes.byref(out))
+    if st != 0:
+        raise TnqeError(st, "tnqe_create failed")
+    return out
+
+
+def tnqe_add_mps(ctx, tensors: Sequence[np.ndarray], U) -> int:
+    ts = [_f64(t) for t in tensors]
+    dims = np.array([1] + [t.shape[2] for t in ts], dtype=np.int32)
+    arr = (ctypes.c_void_p * len(ts))(*[t.ctypes.data for t in ts])
+    U = _f64(U)
+    mid = ctypes.c_int()
+    _check(ctx, load().tnqe_add_mps(ctx, arr, _ptr(dims), _ptr(U), ctypes.byref(mid)))
+    return mid.value
+
+
+def tnqe_reset_mps(ctx):
+    _check(ctx, load().tnqe_reset_mps(ctx))
+
+
+def tnqe_rotate(ctx, i: int, j: int) -> float:
+    d = ctypes.c_double()
+    _check(ctx, load().tnqe_rotate(ctx, i, j, ctypes.byref(d)))
+    return d.value
+
+
+def tnqe_get_rotated(ctx, N: int) -> List[np.ndarray]:
+    dims = np.zeros(N + 1, dtype=np.int32)
+    _check(ctx, load().tnqe_get_rotated(ctx, _ptr(dims), None, 0))
+    total = int(sum(int(dims[s]) * 4 * int(dims[s + 1]) for s in range(N)))
+    buf = np.zeros(max(total, 1))
+    _check(ctx, load().tnqe_get_rotated(ctx, _ptr(dims), _ptr(buf), total))
+    out, o = [], 0
+    for s in range(N):
+        n = int(dims[s]) * 4 * int(dims[s + 1])
+        out.append(buf[o:o + n].reshape(int(dims[s]), 4, int(dims[s + 1])).copy())
+        o += n
+    return out
+
+
+def tnqe_matrix_elements(ctx, pairs: Sequence[Tuple[int, int]], H_out=None, S_out=None):
+    """H_out / S_out: None (host arrays returned) or device pointers as ints."""
+    pr = np.ascontiguousarray(np.asarray(pairs, dtype=np.int32).reshape(-1, 2))
+    n = pr.shape[0]
+    host = H_out is None
+    if host:
+        H_out, S_out = np.zeros(n), np.zeros(n)
+    _check(ctx, load().tnqe_matrix_elements(ctx, _ptr(pr), n, _ptr(H_out), _ptr(S_out)))
+    return (H_out, S_out) if host else None
+
+
+def tnqe_solve(ctx, H, S):
+    H, S = _f64(H), _f64(S)
+    M = H.shape[0]
+    E, C = np.zeros(M), np.zeros((M, M))
+    rank, k1 = ctypes.c_int(), ctypes.c_double()
+    _check(ctx, load().tnqe_solve(ctx, _ptr(H), _ptr(S), M, _ptr(E), _ptr(C), ctypes.byref(rank), ctypes.byref(k1)))
+    return E, C, rank.value, k1.value
+
+
+def tnqe_set_precision(ctx, precision: int):
+    _check(ctx, load().tnqe_set_precision(ctx, precision))
+
+
+def tnqe_last_timing(ctx):
+    t = np.zeros(3)
+    n = ctypes.c_int()
+    _check(ctx, load().tnqe_last_timing(ctx, _ptr(t), ctypes.byref(n)))
+    return t, n.value
+
+
+def tnqe_last_profile(ctx) -> np.ndarray:
+    p = np.zeros(10)
+    _check(ctx, load().tnqe_last_profile(ctx, _ptr(p), 10))
+    return p
+
+
+def tnqe_last_error(ctx) -> str:
+    return load().tnqe_last_error(ctx).decode()
+
+
+def tnqe_destroy(ctx):
+    if ctx:
+        load().tnqe_destroy(ctx)
+
+
+class Context:
+    """Owning wrapper: a context plus the states added to it."""
+
+    def __init__(self, h1, eri, N: int, n_alpha: int, n_beta: int, **opts):
+        o = tnqe_default_options()
+        for k, v in opts.items():
+            setattr(o, k, v)
+        self.N = N
+        self.ctx = tnqe_create(h1, eri, N, n_alpha, n_beta, o)
+
+    def add_mps(self, tensors, U) -> int:
+        return tnqe_add_mps(self.ctx, tensors, U)
+
+    def reset_mps(self):
+        tnqe_reset_mps(self.ctx)
+
+    def rotate(self, i: int, j: int) -> float:
+        return tnqe_rotate(self.ctx, i, j)
+
+    def get_rotated(self):
+        return tnqe_get_rotated(self.ctx, self.N)
+
+    def matrix_elements(self, pairs, H_out=None, S_out=None):
+        return tnqe_matrix_elements(self.ctx, pairs, H_out, S_out)
+
+    def solve(self, H, S):
+        return tnqe_solve(self.ctx, H, S)
+
+    def set_precision(self, p: int):
+        tnqe_set_precision(self.ctx, p)
+
+    def last_timing(self):
+        return tnqe_last_timing(self.ctx)
+
+    def last_profile(self):
+        return tnqe_last_profile(self.ctx)
+
+    def close(self):
+        if self.ctx:
+            tnqe_destroy(self.ctx)
+            self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
