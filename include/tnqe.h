@@ -134,6 +134,44 @@ tnqe_status tnqe_last_timing(const tnqe_ctx* ctx, double* times, int* launches);
  * context stream around each launch and are summed over sites. */
 tnqe_status tnqe_last_profile(const tnqe_ctx* ctx, double* prof, int n);
 
+/* ---------------------------------------------------------------------------
+ * One Givens gate without any allocation.  The paper has no counterpart: this
+ * entry point exists for callers that cannot call cudaMalloc -- code issuing
+ * work while a stream is captured into a CUDA graph (an allocation there ends
+ * or invalidates the capture), programs whose device memory is handed out by
+ * their own pre-reserved pool, and host loops that must not pay allocation
+ * latency.  Everything else in this header allocates through the context.
+ *
+ * Applies G(J^T), J = [[c, -s], [s, c]] on two neighbouring orbitals, to the
+ * two-site tensor A . B and splits it again by a truncated SVD, exactly as one
+ * step of tnqe_rotate:  A [chi_l][4][chi_m], B [chi_m][4][chi_r] in device
+ * memory; q_l, q_m, q_r (host) give every bond index's charge
+ * n_alpha * 16 + n_beta, each bond's indices grouped in ascending charge.
+ * Keeps k = min(chi_max, #{sigma > cutoff * sigma_1}) (at least 1) singular
+ * values; sigma_side 0 puts them into A_out, 1 into B_out.  Writes
+ * A_out [chi_l][4][k] and B_out [k][4][chi_r] (device, capacity for
+ * chi_max), the new bond's charges q_out[k] (host, may be NULL; ascending),
+ * *k_out and *discarded (host; sum of the squared dropped singular values).
+ * chi_l, chi_m, chi_r, chi_max must not exceed TNQE_NOALLOC_MAX_CHI
+ * (TNQE_ERR_ARG otherwise, with the reason in err when err is not NULL).
+ *
+ * Its working storage is one static device array of
+ * TNQE_NOALLOC_SCRATCH_BYTES (about 6.3 MiB) that every GPU loading this
+ * library keeps until the process exits.  The first call on a device resolves
+ * that array's address (cudaGetSymbolAddress) for the current device, so make
+ * that first call before any stream capture begins.  All calls share the one
+ * array: calls that may overlap on the GPU (other streams, other host threads,
+ * the same stream from several captures) race and must be serialised by the
+ * caller.  The call synchronises `stream` (a cudaStream_t, NULL = legacy
+ * default stream) before returning. */
+#define TNQE_NOALLOC_MAX_CHI 128
+#define TNQE_NOALLOC_SCRATCH_BYTES 6569984
+tnqe_status tnqe_apply_gate_noalloc(const double* A, const double* B, int chi_l, int chi_m, int chi_r,
+                                    const int* q_l, const int* q_m, const int* q_r, double c, double s,
+                                    int sigma_side, int chi_max, double cutoff, int max_sweeps,
+                                    double* A_out, double* B_out, int* q_out, int* k_out,
+                                    double* discarded, void* stream, char* err, int err_len);
+
 /* Human-readable description of the last error on this context. */
 const char* tnqe_last_error(const tnqe_ctx* ctx);
 

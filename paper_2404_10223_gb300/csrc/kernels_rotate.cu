@@ -496,3 +496,436 @@ int launch_rotate(const RotDesc* d_descs, int npairs, int smem_bytes, void* stre
 }
 
 }  // namespace tnqe
+
+// =============================================================================
+// One Givens gate with scratch in a static device array (no allocation).
+//
+// For callers that cannot call cudaMalloc: code running while a stream is
+// being captured into a CUDA graph (where an allocation would end or break
+// the capture), host programs whose device memory is fully reserved up front
+// by their own pool, and host code that must not pay allocation latency
+// inside a time-critical loop.  The caller passes device buffers for the
+// inputs and outputs; all intermediate storage of the step (two-site tensor,
+// SVD blocks, block bookkeeping) lives in tnqe_gate_scratch below, which
+// every GPU that loads this library holds until the process exits.
+// =============================================================================
+
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+
+#include "../../include/tnqe.h"
+
+namespace tnqe {
+namespace {
+
+constexpr int NA_CHI = TNQE_NOALLOC_MAX_CHI;
+constexpr size_t NA_HDR_BYTES = 16384;
+constexpr size_t NA_META_INTS = 65536;
+constexpr size_t NA_BLOCK_DOUBLES = 16ull * NA_CHI * NA_CHI;   // theta, block matrices, block rotations
+
+struct NaHeader {
+  SectorTable secL, secM, secR, secOut;
+  double G[256];
+  const double* A;
+  const double* B;
+  double* Aout;
+  double* Bout;
+  double cutoff;
+  double disc;
+  int chl, chm, chr, chi_max, side, max_sweeps;
+  int k_out, status;
+};
+static_assert(sizeof(NaHeader) <= NA_HDR_BYTES, "header does not fit");
+static_assert(NA_HDR_BYTES + NA_META_INTS * 4 + 3 * NA_BLOCK_DOUBLES * 8 == TNQE_NOALLOC_SCRATCH_BYTES,
+              "scratch layout and TNQE_NOALLOC_SCRATCH_BYTES disagree");
+
+}  // namespace
+
+// The scratch of tnqe_apply_gate_noalloc.  Host code may only use its address
+// as resolved by cudaGetSymbolAddress on the current device (gate_scratch_ptr).
+static __device__ __align__(256) unsigned char tnqe_gate_scratch[TNQE_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+
+__global__ void __launch_bounds__(ROT_THREADS) gate_static_kernel(unsigned char* __restrict__ scratch) {
+  NaHeader& H = *reinterpret_cast<NaHeader*>(scratch);
+  int* meta = reinterpret_cast<int*>(scratch + NA_HDR_BYTES);
+  double* theta = reinterpret_cast<double*>(scratch + NA_HDR_BYTES + NA_META_INTS * 4);
+  double* wbuf = theta + NA_BLOCK_DOUBLES;
+  double* qbuf = wbuf + NA_BLOCK_DOUBLES;
+  const int tid = threadIdx.x;
+  ThetaBlk* tb = reinterpret_cast<ThetaBlk*>(meta);
+  const long long tb_cap = (long long)NA_META_INTS / 2 / (long long)(sizeof(ThetaBlk) / sizeof(int));
+  NewBlk* nb = reinterpret_cast<NewBlk*>(meta + NA_META_INTS / 2);
+  const long long nb_cap = (long long)NA_META_INTS / 2 / (long long)(sizeof(NewBlk) / sizeof(int));
+
+  __shared__ int lutL[QSPACE], lutM[QSPACE], lutR[QSPACE];
+  __shared__ int gnz_n[16], gnz_k[16][16];
+  __shared__ double gnz_v[16][16];
+  __shared__ double sig[MAXSIG];
+  __shared__ unsigned char sig_keep[MAXSIG];
+  __shared__ int s_nblk, s_nnew, s_total, s_nsig, s_keep, s_flag, s_status;
+  __shared__ double s_red[ROT_WARPS];
+
+  const SectorTable& secL = H.secL;
+  const SectorTable& secM = H.secM;
+  const SectorTable& secR = H.secR;
+  const int chl = H.chl, chm = H.chm, chr = H.chr, side = H.side;
+  const double* Lt = H.A;
+  const double* Rt = H.B;
+  for (int x = tid; x < QSPACE; x += ROT_THREADS) {
+    lutL[x] = -1;
+    lutM[x] = -1;
+    lutR[x] = -1;
+  }
+  if (tid == 0) s_status = 0;
+  __syncthreads();
+  for (int x = tid; x < secL.nsec; x += ROT_THREADS) lutL[secL.q[x]] = x;
+  for (int x = tid; x < secM.nsec; x += ROT_THREADS) lutM[secM.q[x]] = x;
+  for (int x = tid; x < secR.nsec; x += ROT_THREADS) lutR[secR.q[x]] = x;
+  if (tid < 16) {
+    int c = 0;
+    for (int K = 0; K < 16; ++K) {
+      const double v = H.G[tid * 16 + K];
+      if (v != 0.0) {
+        gnz_k[tid][c] = K;
+        gnz_v[tid][c] = v;
+        ++c;
+      }
+    }
+    gnz_n[tid] = c;
+  }
+  __syncthreads();
+  // two-site tensor, charge-allowed blocks only
+  if (tid == 0) {
+    int nblk = 0, start = 0;
+    for (int sL = 0; sL < secL.nsec; ++sL)
+      for (int k1 = 0; k1 < 4; ++k1) {
+        const int qM = qadd(secL.q[sL], local_charge(k1));
+        const int sM = qM < 0 ? -1 : lutM[qM];
+        if (sM < 0) continue;
+        for (int k2 = 0; k2 < 4; ++k2) {
+          const int qR = qadd(qM, local_charge(k2));
+          const int sR = qR < 0 ? -1 : lutR[qR];
+          if (sR < 0) continue;
+          if (nblk < tb_cap) tb[nblk] = ThetaBlk{sL, sM, sR, k1, k2, start};
+          ++nblk;
+          start += secL.dim[sL] * secR.dim[sR];
+        }
+      }
+    if (nblk > tb_cap) {
+      s_status |= STATUS_OVERFLOW;
+      nblk = (int)tb_cap;
+    }
+    s_nblk = nblk;
+    s_total = start;
+  }
+  __syncthreads();
+  for (int idx = tid; idx < s_total; idx += ROT_THREADS) {
+    int lo = 0, hi = s_nblk - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (tb[mid].start <= idx) lo = mid; else hi = mid - 1;
+    }
+    const ThetaBlk B = tb[lo];
+    const int dR = secR.dim[B.sR];
+    const int l = secL.off[B.sL] + (idx - B.start) / dR, r = secR.off[B.sR] + (idx - B.start) % dR;
+    const int m0 = secM.off[B.sM], m1 = m0 + secM.dim[B.sM];
+    const double* lrow = Lt + ((size_t)l * 4 + B.k1) * chm;
+    const double* rcol = Rt + (size_t)B.k2 * chr + r;
+    double acc = 0.0;
+    for (int m = m0; m < m1; ++m) acc = fma(lrow[m], rcol[(size_t)m * 4 * chr], acc);
+    theta[(((size_t)l * 4 + B.k1) * 4 + B.k2) * chr + r] = acc;
+  }
+  // blocks of the new middle bond
+  if (tid == 0) {
+    int nnew = 0, nsig = 0;
+    long long wofs = 0, qofs = 0;
+    for (int q = 0; q < QSPACE; ++q) {
+      NewBlk B;
+      B.q = q;
+      int nr = 0, nc = 0;
+      for (int k = 0; k < 4; ++k) {
+        const int qL = qsub(q, local_charge(k));
+        const int sL = qL < 0 ? -1 : lutL[qL];
+        B.rowsec[k] = sL;
+        B.rowoff[k] = nr;
+        if (sL >= 0) nr += secL.dim[sL];
+        const int qR = qadd(q, local_charge(k));
+        const int sR = qR < 0 ? -1 : lutR[qR];
+        B.colsec[k] = sR;
+        B.coloff[k] = nc;
+        if (sR >= 0) nc += secR.dim[sR];
+      }
+      if (nr == 0 || nc == 0) continue;
+      B.nr = nr;
+      B.nc = nc;
+      const int mm = nr > nc ? nr : nc, nn = nr > nc ? nc : nr;
+      B.wofs = wofs;
+      B.qofs = qofs;
+      B.sofs = nsig;
+      B.kept = 0;
+      B.newoff = 0;
+      B.scale = 1.0;
+      wofs += (long long)mm * nn;
+      qofs += (long long)nn * nn;
+      nsig += nn;
+      if (nnew < nb_cap && nsig <= MAXSIG) nb[nnew] = B;
+      ++nnew;
+    }
+    if (nnew > nb_cap || nsig > MAXSIG) {
+      s_status |= STATUS_OVERFLOW;
+      nnew = 0;
+      nsig = 0;
+    }
+    s_nnew = nnew;
+    s_nsig = nsig;
+  }
+  __syncthreads();
+  const int nnew = s_nnew;
+  for (int b = 0; b < nnew; ++b) {
+    const NewBlk B = nb[b];
+    const bool trans = B.nc > B.nr;
+    const int m = trans ? B.nc : B.nr, n = trans ? B.nr : B.nc;
+    double* W = wbuf + B.wofs;
+    double* Q = qbuf + B.qofs;
+    for (int idx = tid; idx < m * n; idx += ROT_THREADS) {
+      const int wi = idx % m, wj = idx / m;
+      const int br = trans ? wj : wi, bc = trans ? wi : wj;
+      int k1p = 3, k2p = 3;
+      while (k1p > 0 && (B.rowsec[k1p] < 0 || B.rowoff[k1p] > br)) --k1p;
+      while (k2p > 0 && (B.colsec[k2p] < 0 || B.coloff[k2p] > bc)) --k2p;
+      const int sL = B.rowsec[k1p], sR = B.colsec[k2p];
+      const int l = secL.off[sL] + (br - B.rowoff[k1p]);
+      const int r = secR.off[sR] + (bc - B.coloff[k2p]);
+      const int Kp = k1p * 4 + k2p;
+      double acc = 0.0;
+      for (int e = 0; e < gnz_n[Kp]; ++e) {
+        const int K = gnz_k[Kp][e];
+        const int k1 = K >> 2, k2 = K & 3;
+        const int qM = qadd(secL.q[sL], local_charge(k1));
+        if (qM < 0 || lutM[qM] < 0) continue;
+        acc = fma(gnz_v[Kp][e], theta[(((size_t)l * 4 + k1) * 4 + k2) * chr + r], acc);
+      }
+      W[idx] = acc;
+    }
+    __syncthreads();
+    double mx = 0.0;
+    for (int idx = tid; idx < m * n; idx += ROT_THREADS) mx = fmax(mx, fabs(W[idx]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((tid & 31) == 0) s_red[tid >> 5] = mx;
+    __syncthreads();
+    double bmax = 0.0;
+    for (int w = 0; w < ROT_WARPS; ++w) bmax = fmax(bmax, s_red[w]);
+    const double scale = bmax > 0.0 ? bmax : 1.0;
+    for (int idx = tid; idx < m * n; idx += ROT_THREADS) W[idx] *= 1.0 / scale;
+    if (tid == 0) nb[b].scale = scale;
+    __syncthreads();
+    if (jacobi_block(W, Q, m, n, H.max_sweeps, &s_flag) && tid == 0) s_status |= STATUS_NOCONV;
+    for (int j = 0; j < n; ++j) {
+      double acc = 0.0;
+      for (int u = tid; u < m; u += ROT_THREADS) acc = fma(W[(size_t)j * m + u], W[(size_t)j * m + u], acc);
+      acc = warp_sum(acc);
+      if ((tid & 31) == 0) s_red[tid >> 5] = acc;
+      __syncthreads();
+      if (tid == 0) {
+        double t = 0.0;
+        for (int w = 0; w < ROT_WARPS; ++w) t += s_red[w];
+        sig[B.sofs + j] = sqrt(t) * scale;
+      }
+      __syncthreads();
+    }
+  }
+  // truncation: k = min(chi_max, #{sigma > cutoff sigma_1}), at least 1
+  const int nsig = s_nsig;
+  if (tid == 0) {
+    double smax = 0.0;
+    for (int x = 0; x < nsig; ++x) smax = fmax(smax, sig[x]);
+    int above = 0;
+    for (int x = 0; x < nsig; ++x) above += (sig[x] > H.cutoff * smax) ? 1 : 0;
+    int keep = above < H.chi_max ? above : H.chi_max;
+    if (keep < 1) keep = 1;
+    if (keep > nsig) keep = nsig;
+    s_keep = keep;
+  }
+  __syncthreads();
+  for (int x = tid; x < nsig; x += ROT_THREADS) {
+    const double v = sig[x];
+    int rank = 0;
+    for (int y = 0; y < nsig; ++y) rank += (sig[y] > v || (sig[y] == v && y < x)) ? 1 : 0;
+    sig_keep[x] = rank < s_keep ? 1 : 0;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double disc = 0.0;
+    for (int x = 0; x < nsig; ++x)
+      if (!sig_keep[x]) disc += sig[x] * sig[x];
+    H.disc = disc;
+    int off = 0;
+    SectorTable& nt = H.secOut;
+    nt.nsec = 0;
+    for (int b = 0; b < nnew; ++b) {
+      int kept = 0;
+      for (int j = 0; j < (nb[b].nr < nb[b].nc ? nb[b].nr : nb[b].nc); ++j) kept += sig_keep[nb[b].sofs + j];
+      nb[b].kept = kept;
+      nb[b].newoff = off;
+      if (kept > 0) {
+        nt.q[nt.nsec] = nb[b].q;
+        nt.off[nt.nsec] = off;
+        nt.dim[nt.nsec] = kept;
+        ++nt.nsec;
+      }
+      off += kept;
+    }
+    H.k_out = off;
+  }
+  __syncthreads();
+  const int knew = H.k_out;
+  double* Ao = H.Aout;
+  double* Bo = H.Bout;
+  for (long long x = tid; x < (long long)chl * 4 * knew; x += ROT_THREADS) Ao[x] = 0.0;
+  for (long long x = tid; x < (long long)knew * 4 * chr; x += ROT_THREADS) Bo[x] = 0.0;
+  __syncthreads();
+  for (int b = 0; b < nnew; ++b) {
+    const NewBlk B = nb[b];
+    if (B.kept == 0) continue;
+    const bool trans = B.nc > B.nr;
+    const int m = trans ? B.nc : B.nr, n = trans ? B.nr : B.nc;
+    const double* W = wbuf + B.wofs;
+    const double* Q = qbuf + B.qofs;
+    const double bs = B.scale;
+    int newidx = B.newoff;
+    for (int j = 0; j < n; ++j) {
+      if (!sig_keep[B.sofs + j]) continue;
+      const double sj = sig[B.sofs + j];
+      const double inv = sj > 0.0 ? 1.0 / sj : 0.0;
+      for (int br = tid; br < B.nr; br += ROT_THREADS) {
+        int k1p = 3;
+        while (k1p > 0 && (B.rowsec[k1p] < 0 || B.rowoff[k1p] > br)) --k1p;
+        const int l = secL.off[B.rowsec[k1p]] + (br - B.rowoff[k1p]);
+        double v;
+        if (!trans) v = (side == 0) ? W[(size_t)j * m + br] * bs : W[(size_t)j * m + br] * bs * inv;
+        else v = (side == 0) ? Q[(size_t)j * n + br] * sj : Q[(size_t)j * n + br];
+        Ao[((size_t)l * 4 + k1p) * knew + newidx] = v;
+      }
+      for (int bc = tid; bc < B.nc; bc += ROT_THREADS) {
+        int k2p = 3;
+        while (k2p > 0 && (B.colsec[k2p] < 0 || B.coloff[k2p] > bc)) --k2p;
+        const int r = secR.off[B.colsec[k2p]] + (bc - B.coloff[k2p]);
+        double v;
+        if (!trans) v = (side == 0) ? Q[(size_t)j * n + bc] : Q[(size_t)j * n + bc] * sj;
+        else v = (side == 0) ? W[(size_t)j * m + bc] * bs * inv : W[(size_t)j * m + bc] * bs;
+        Bo[((size_t)newidx * 4 + k2p) * chr + r] = v;
+      }
+      ++newidx;
+    }
+  }
+  if (tid == 0) H.status = s_status;
+}
+
+constexpr int NA_MAX_DEVICES = 64;
+std::mutex na_mutex;
+void* na_ptr[NA_MAX_DEVICES] = {nullptr};
+
+// Device address of tnqe_gate_scratch on the current device, resolved once per device.
+cudaError_t gate_scratch_ptr(unsigned char** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= NA_MAX_DEVICES) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(na_mutex);
+  if (!na_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, tnqe_gate_scratch);
+    if (e != cudaSuccess) return e;
+    na_ptr[dev] = p;
+  }
+  *out = static_cast<unsigned char*>(na_ptr[dev]);
+  return cudaSuccess;
+}
+
+bool na_sectors(const int* q, int n, SectorTable& T) {
+  T.nsec = 0;
+  for (int x = 0; x < n; ++x) {
+    const int qa = q[x] / QSTRIDE, qb = q[x] % QSTRIDE;
+    if (q[x] < 0 || qa >= QSTRIDE - 1 || qb >= QSTRIDE - 1) return false;
+    if (x > 0 && q[x] < q[x - 1]) return false;           // indices must be grouped by ascending charge
+    if (T.nsec == 0 || T.q[T.nsec - 1] != q[x]) {
+      if (T.nsec >= MAXSEC) return false;
+      T.q[T.nsec] = q[x];
+      T.off[T.nsec] = x;
+      T.dim[T.nsec] = 0;
+      ++T.nsec;
+    }
+    ++T.dim[T.nsec - 1];
+  }
+  return true;
+}
+
+tnqe_status na_fail(char* err, int err_len, tnqe_status st, const char* msg) {
+  if (err && err_len > 0) {
+    std::strncpy(err, msg, (size_t)err_len - 1);
+    err[err_len - 1] = '\0';
+  }
+  return st;
+}
+
+}  // namespace
+}  // namespace tnqe
+
+extern "C" tnqe_status tnqe_apply_gate_noalloc(const double* A, const double* B, int chi_l, int chi_m, int chi_r,
+                                               const int* q_l, const int* q_m, const int* q_r, double c, double s,
+                                               int sigma_side, int chi_max, double cutoff, int max_sweeps,
+                                               double* A_out, double* B_out, int* q_out, int* k_out,
+                                               double* discarded, void* stream, char* err, int err_len) {
+  using namespace tnqe;
+  if (!A || !B || !A_out || !B_out || !q_l || !q_m || !q_r || !k_out)
+    return na_fail(err, err_len, TNQE_ERR_ARG, "null argument");
+  if (chi_l < 1 || chi_m < 1 || chi_r < 1 || chi_max < 1 || chi_l > NA_CHI || chi_m > NA_CHI || chi_r > NA_CHI ||
+      chi_max > NA_CHI)
+    return na_fail(err, err_len, TNQE_ERR_ARG,
+                   "bond dimensions must be in [1, TNQE_NOALLOC_MAX_CHI = 128] for the no-allocation gate");
+  if (sigma_side != 0 && sigma_side != 1) return na_fail(err, err_len, TNQE_ERR_ARG, "sigma_side must be 0 or 1");
+  if (!(cutoff >= 0.0) || max_sweeps < 1) return na_fail(err, err_len, TNQE_ERR_ARG, "bad cutoff or sweep limit");
+  NaHeader h;
+  std::memset(&h, 0, sizeof(h));
+  if (!na_sectors(q_l, chi_l, h.secL) || !na_sectors(q_m, chi_m, h.secM) || !na_sectors(q_r, chi_r, h.secR))
+    return na_fail(err, err_len, TNQE_ERR_ARG,
+                   "bond charges must be n_alpha*16+n_beta (each below 15) in ascending order");
+  gate_matrix(c, s, h.G);
+  h.A = A;
+  h.B = B;
+  h.Aout = A_out;
+  h.Bout = B_out;
+  h.cutoff = cutoff;
+  h.chl = chi_l;
+  h.chm = chi_m;
+  h.chr = chi_r;
+  h.chi_max = chi_max;
+  h.side = sigma_side;
+  h.max_sweeps = max_sweeps;
+  unsigned char* scratch = nullptr;
+  cudaError_t e = gate_scratch_ptr(&scratch);
+  if (e != cudaSuccess) return na_fail(err, err_len, TNQE_ERR_CUDA, cudaGetErrorString(e));
+  cudaStream_t st = (cudaStream_t)stream;
+  e = cudaMemcpyAsync(scratch, &h, sizeof(h), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) {
+    gate_static_kernel<<<1, ROT_THREADS, 0, st>>>(scratch);
+    e = cudaGetLastError();
+  }
+  NaHeader r;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&r, scratch, sizeof(r), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return na_fail(err, err_len, TNQE_ERR_CUDA, cudaGetErrorString(e));
+  *k_out = r.k_out;
+  if (discarded) *discarded = r.disc;
+  if (q_out)
+    for (int t = 0; t < r.secOut.nsec; ++t)
+      for (int x = 0; x < r.secOut.dim[t]; ++x) q_out[r.secOut.off[t] + x] = r.secOut.q[t];
+  if (r.status & STATUS_OVERFLOW) return na_fail(err, err_len, TNQE_ERR_STATE, "gate bookkeeping overflow");
+  if (r.status & STATUS_NOCONV)
+    return na_fail(err, err_len, TNQE_ERR_NOCONV, "Jacobi SVD hit the sweep limit (outputs written)");
+  return na_fail(err, err_len, TNQE_OK, "");
+}

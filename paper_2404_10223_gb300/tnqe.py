@@ -37,7 +37,7 @@ class tnqe_options(ctypes.Structure):
 
 
 EXPORTED = ["tnqe_default_options", "tnqe_create", "tnqe_add_mps", "tnqe_reset_mps", "tnqe_rotate",
-            "tnqe_get_rotated", "tnqe_matrix_elements", "tnqe_solve", "tnqe_set_precision", "tnqe_last_timing", "tnqe_last_profile",
+            "tnqe_get_rotated", "tnqe_matrix_elements", "tnqe_solve", "tnqe_set_precision", "tnqe_last_timing", "tnqe_last_profile", "tnqe_apply_gate_noalloc",
             "tnqe_last_error", "tnqe_destroy"]
 
 _lib = None
@@ -63,6 +63,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.tnqe_set_precision.argtypes = [P, I]
     lib.tnqe_last_timing.argtypes = [P, P, ctypes.POINTER(I)]
     lib.tnqe_last_profile.argtypes = [P, P, I]
+    lib.tnqe_apply_gate_noalloc.argtypes = [P, P, I, I, I, P, P, P, D, D, I, I, D, I, P, P, P,
+                                            ctypes.POINTER(I), ctypes.POINTER(D), P, ctypes.c_char_p, I]
     lib.tnqe_last_error.argtypes = [P]
     lib.tnqe_last_error.restype = ctypes.c_char_p
     lib.tnqe_destroy.argtypes = [P]
@@ -176,6 +178,23 @@ def tnqe_last_profile(ctx) -> np.ndarray:
     p = np.zeros(10)
     _check(ctx, load().tnqe_last_profile(ctx, _ptr(p), 10))
     return p
+
+
+def tnqe_apply_gate_noalloc(A: int, B: int, chi_l: int, chi_m: int, chi_r: int, q_l, q_m, q_r, c: float,
+                            s: float, sigma_side: int, chi_max: int, cutoff: float, max_sweeps: int,
+                            A_out: int, B_out: int, stream: int = 0):
+    """A, B, A_out, B_out: device pointers (ints).  Returns (k, q_out, discarded)."""
+    ql, qm, qr = (np.ascontiguousarray(q, dtype=np.int32) for q in (q_l, q_m, q_r))
+    q_out = np.zeros(chi_max, dtype=np.int32)
+    k, disc = ctypes.c_int(), ctypes.c_double()
+    err = ctypes.create_string_buffer(256)
+    st = load().tnqe_apply_gate_noalloc(ctypes.c_void_p(A), ctypes.c_void_p(B), chi_l, chi_m, chi_r, _ptr(ql),
+                                        _ptr(qm), _ptr(qr), c, s, sigma_side, chi_max, cutoff, max_sweeps,
+                                        ctypes.c_void_p(A_out), ctypes.c_void_p(B_out), _ptr(q_out),
+                                        ctypes.byref(k), ctypes.byref(disc), ctypes.c_void_p(stream), err, 256)
+    if st != 0:
+        raise TnqeError(st, err.value.decode())
+    return k.value, q_out[:k.value].copy(), disc.value
 
 
 def tnqe_last_error(ctx) -> str:
