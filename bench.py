@@ -231,21 +231,70 @@ def run_native(args):
     K = args.steps
     peaks, peak_src = load_peaks()
     fp64_peak = peaks["bf16_tflops"] * (1.25 / 2250.0)          # nominal FP64 : BF16 dense ratio
-    kern = {
-        "rotate_pairs_kernel": (prof[0] / K, prof[4] / K, "alu", fp64_peak, "TFLOP/s"),
-        "gemm_f64_grouped(stage1)": (prof[1] / K, prof[5] / K, "alu", fp64_peak, "TFLOP/s"),
-        "spmm_f64_grouped": (prof[2] / K, prof[6] / K, "hbm", peaks["hbm_gbs"], "GB/s"),
-        "gemm_f64_grouped(stage3)": (prof[3] / K, prof[7] / K, "alu", fp64_peak, "TFLOP/s"),
-    }
+    if args.precision == "fp64":
+        kern = {
+            "rotate_pairs_kernel": (prof[0] / K, prof[4] / K, "alu", fp64_peak, "TFLOP/s"),
+            "gemm_f64_grouped(stage1)": (prof[1] / K, prof[5] / K, "alu", fp64_peak, "TFLOP/s"),
+            "spmm_f64_grouped": (prof[2] / K, prof[6] / K, "hbm", peaks["hbm_gbs"], "GB/s"),
+            "gemm_f64_grouped(stage3)": (prof[3] / K, prof[7] / K, "alu", fp64_peak, "TFLOP/s"),
+        }
+    else:
+        # TF32x3: three TF32 MMAs per product; useful FLOPs against the TF32 dense peak
+        # (measured BF16 burst x nominal TF32:BF16 = 1.1 : 2.25) divided by 3
+        tf32_eff = peaks["bf16_tflops"] * (1.1 / 2.25) / 3.0
+        kern = {
+            "rotate_pairs_kernel": (prof[0] / K, prof[4] / K, "alu", fp64_peak, "TFLOP/s"),
+            "gemm_tf32x3_kernel(stage1)": (prof[1] / K, prof[5] / K, "tensor", tf32_eff, "TFLOP/s"),
+            "spmm_t_f32_kernel": (prof[2] / K, prof[6] / K, "hbm", peaks["hbm_gbs"], "GB/s"),
+            "gemm_tf32x3_kernel(stage3)": (prof[3] / K, prof[7] / K, "tensor", tf32_eff, "TFLOP/s"),
+        }
     top = max(kern, key=lambda k: kern[k][0])
     t_ms, work, bound, peak, unit = kern[top]
     achieved = (work / (t_ms / 1e3)) / (1e12 if unit == "TFLOP/s" else 1e9) if t_ms > 0 else 0.0
     roof = {"kernel": top, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
             "frac": achieved / peak if peak else None, "traffic": None,
-            "peak_source": ("FP64 = measured bf16 burst x 1.25/2250 (nominal ratio)" if unit == "TFLOP/s"
-                            else f"hbm_gbs ({peak_src})"),
+            "peak_source": ({"alu": "FP64 = measured bf16 burst x 1.25/2250 (nominal ratio)",
+                             "tensor": "TF32x3 useful = measured bf16 burst x 1.1/2.25 / 3",
+                             "hbm": f"hbm_gbs ({peak_src})"}[bound]),
             "ms_per_step": t_ms, "work_per_step": work,
             "breakdown_ms": {k: v[0] for k, v in kern.items()}}
+    # the plain FP64 form on the same workload, and |dE| of this precision against it
+    Hh = Hd.cpu().numpy().copy()
+    Sh = Sd.cpu().numpy().copy()
+    fp64 = None
+    if args.precision != "fp64" and args.fp64_steps > 0:
+        g.set_precision(0)
+        step()
+        torch.cuda.synchronize()
+        f_ms = []
+        for _ in range(args.fp64_steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(1.0)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            f_ms.append(e0.elapsed_time(e1))
+        H64 = Hd.cpu().numpy().copy()
+        S64 = Sd.cpu().numpy().copy()
+        g.set_precision(PREC[args.precision])
+
+        def energy(Hv, Sv):
+            Mm = w.M
+            Hm, Sm = np.zeros((Mm, Mm)), np.zeros((Mm, Mm))
+            for (i, j), h, s in zip(pairs, Hv, Sv):
+                Hm[i, j] = Hm[j, i] = h
+                Sm[i, j] = Sm[j, i] = s
+            return g.solve(Hm, Sm)[0][0]
+        e_fast, e_64 = energy(Hh, Sh), energy(H64, S64)
+        f_mean = statistics.mean(f_ms)
+        fp64 = {"value": npairs * world / (max_over_ranks(f_mean, world) / 1000.0), "unit": UNIT,
+                "ms_per_step": f_mean, "steps": args.fp64_steps,
+                "speedup": (max_over_ranks(f_mean, world) / ms_max),
+                "dE_Ha": abs(e_fast - e_64), "E_fp64": e_64,
+                "max_dH": float(np.abs(Hh - H64).max()), "max_dS": float(np.abs(Sh - S64).max())}
     # end to end through host buffers: H2D of every state, D2H of H and S
     pinned = []
     h2d = 0
@@ -272,7 +321,7 @@ def run_native(args):
             "dtype": DTYPE[args.precision], "data": "synthetic", "config": config_of(w, args.precision),
             "clocks": clk, "gpu_launches": launches,
             "e2e": {"value": e2e_v, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": 16 * npairs},
-            "roofline": roof}
+            "roofline": roof, "plain_fp64_gpu": fp64}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, el, done = oracle_sample(w, 30.0)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cpu_threads(), "kind": "oracle",
@@ -290,7 +339,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--workload", default="n14_chi128")
-    ap.add_argument("--precision", default="fp64", choices=list(PREC))
+    ap.add_argument("--precision", default="tf32x3", choices=list(PREC))
+    ap.add_argument("--fp64-steps", type=int, default=2, help="timed steps of the plain FP64 form (0 = skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":

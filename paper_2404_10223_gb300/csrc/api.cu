@@ -12,8 +12,11 @@
 #include <string>
 #include <vector>
 
+#include <cudaTypedefs.h>
+
 #include "../../include/tnqe.h"
 #include "internal.h"
+#include "tc_gemm.cuh"
 
 using namespace tnqe;
 
@@ -86,6 +89,7 @@ struct DevMps {
   Mpo mpo;                               // host copy (dims, CSR)
   std::vector<int*> d_rowptr, d_col;
   std::vector<double*> d_val;
+  std::vector<float*> d_val32;
   std::vector<void*> owned;
   void free_all() {
     for (void* p : owned) cudaFree(p);
@@ -117,6 +121,7 @@ struct tnqe_ctx {
   DBuf rot_work, rot_scratch, rot_meta, rot_small, rot_desc;
   // contraction workspace
   DBuf con_ws, con_desc, con_out;
+  DBuf tc_ws, tc_desc, tc_err;
   // last tnqe_rotate result
   int kept_pair_valid = 0;
   std::vector<int> kept_dims;
@@ -234,7 +239,7 @@ void run_rotations(tnqe_ctx* c, const std::vector<std::pair<int, int>>& pairs, R
     work_total += tot;
     rb.scratch_base.push_back(scratch_total);
     rb.scratch_len.push_back(th);
-    scratch_total += 3 * th;
+    scratch_total += 6 * th;
   }
   // small per-pair arrays: dims (N+1 ints), caps, offsets, sectors, disc, status
   auto al256 = [](size_t x) { return (x + 255) & ~(size_t)255; };
@@ -288,9 +293,14 @@ void run_rotations(tnqe_ctx* c, const std::vector<std::pair<int, int>>& pairs, R
     d.gate_site = pl->d_site;
     d.gate_side = pl->d_side;
     double* sb = c->rot_scratch.as<double>() + rb.scratch_base[k];
+    const long long th = rb.scratch_len[k];
     d.theta = sb;
-    d.wbuf = sb + rb.scratch_len[k];
-    d.qbuf = sb + 2 * rb.scratch_len[k];
+    d.bbuf = sb + th;
+    d.wbuf = sb + 2 * th;
+    d.qbuf = sb + 3 * th;
+    d.tbuf = sb + 4 * th;
+    d.w32 = reinterpret_cast<float*>(sb + 5 * th);
+    d.q32 = d.w32 + th;
     d.meta = c->rot_meta.as<int>() + META_INTS * k;
     d.meta_cap = META_INTS;
     d.discarded = ddisc;
@@ -544,6 +554,259 @@ void run_contractions(tnqe_ctx* c, const std::vector<std::pair<int, int>>& pairs
   }
 }
 
+// ----------------------------------------------------------------------------- split-precision contraction
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    cudaDriverEntryPointQueryResult q;
+    void* p = nullptr;
+    CK(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q));
+    if (q != cudaDriverEntryPointSuccess || !p) throw Error(TNQE_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
+    fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+// 2-D FP32 tensor map: rows x cols (cols contiguous, row stride ld floats), 32-column boxes
+void encode_map(CUtensorMap* map, const float* base, long long rows, long long cols, long long ld, int box_rows) {
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)ld * 4};
+  cuuint32_t box[2] = {(cuuint32_t)TC_BK, (cuuint32_t)box_rows};
+  cuuint32_t es[2] = {1, 1};
+  const CUresult r = tensor_map_encoder()(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims,
+                                          strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                                          CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) throw Error(TNQE_ERR_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
+}
+
+inline long long al64(long long x) { return (x + 63) & ~63LL; }   // floats -> 256-byte aligned offsets
+inline int ld4(int x) { return (x + 3) & ~3; }
+
+void run_contractions_tc(tnqe_ctx* c, const std::vector<std::pair<int, int>>& pairs, const std::vector<KetView>& kets,
+                         double* d_H, double* d_S) {
+  const int N = c->N;
+  const int np = (int)pairs.size();
+  // per-pair FP32 workspace: two environments, X, Yt, packed ket / bra sites
+  std::vector<long long> envsz(np), xsz(np), ysz(np), packsz(np);
+  for (int p = 0; p < np; ++p) {
+    const DevMps& bi = *c->mps[pairs[p].first];
+    const KetView& kv = kets[p];
+    long long e = 4, x = 4, y = 4, pk = 0;
+    for (int t = 0; t <= N; ++t) e = std::max(e, (long long)bi.dims[t] * bi.mpo.dims[t] * ld4(kv.dims[t]));
+    for (int t = 0; t < N; ++t) {
+      x = std::max(x, (long long)bi.dims[t] * bi.mpo.dims[t] * 4 * kv.dims[t + 1]);
+      y = std::max(y, (long long)bi.mpo.dims[t + 1] * kv.dims[t + 1] * 4 * bi.dims[t]);
+      pk += al64((long long)4 * kv.dims[t + 1] * ld4(kv.dims[t])) + al64((long long)bi.dims[t + 1] * 4 * bi.dims[t]);
+    }
+    envsz[p] = al64(e);
+    xsz[p] = al64(x);
+    ysz[p] = al64(y);
+    packsz[p] = pk;
+  }
+  size_t freeb = 0, totalb = 0;
+  CK(cudaMemGetInfo(&freeb, &totalb));
+  const double budget = 0.6 * (double)(freeb + c->tc_ws.cap);
+  c->tc_err.ensure(256);
+  CK(cudaMemsetAsync(c->tc_err.p, 0, sizeof(int), c->stream));
+  size_t p0 = 0;
+  while (p0 < (size_t)np) {
+    size_t p1 = p0;
+    double need = 0.0;
+    while (p1 < (size_t)np) {
+      const double add = 4.0 * (2.0 * envsz[p1] + xsz[p1] + ysz[p1] + packsz[p1]);
+      if (p1 > p0 && need + add > budget) break;
+      need += add;
+      ++p1;
+    }
+    const int nw = (int)(p1 - p0);
+    c->tc_ws.ensure((size_t)need + 1024);
+    float* base = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(c->tc_ws.p) + 255) & ~(uintptr_t)255);
+    std::vector<float*> env0(nw), env1(nw), X(nw), Y(nw);
+    std::vector<std::vector<float*>> ketT(nw, std::vector<float*>(N)), braT(nw, std::vector<float*>(N));
+    std::vector<PackDesc> packs;
+    std::vector<long long> packpre;
+    long long packtot = 0;
+    {
+      long long o = 0;
+      for (int w = 0; w < nw; ++w) {
+        const int p = (int)p0 + w;
+        const DevMps& bi = *c->mps[pairs[p].first];
+        const KetView& kv = kets[p];
+        env0[w] = base + o; o += envsz[p];
+        env1[w] = base + o; o += envsz[p];
+        X[w] = base + o; o += xsz[p];
+        Y[w] = base + o; o += ysz[p];
+        for (int t = 0; t < N; ++t) {
+          ketT[w][t] = base + o;
+          o += al64((long long)4 * kv.dims[t + 1] * ld4(kv.dims[t]));
+          braT[w][t] = base + o;
+          o += al64((long long)bi.dims[t + 1] * 4 * bi.dims[t]);
+          PackDesc pk{kv.base + kv.off[t], ketT[w][t], kv.dims[t], kv.dims[t + 1], ld4(kv.dims[t]), 0};
+          packpre.push_back(packtot);
+          packtot += (long long)kv.dims[t] * 4 * kv.dims[t + 1];
+          packs.push_back(pk);
+          PackDesc pb{bi.d_t + bi.off[t], braT[w][t], bi.dims[t], bi.dims[t + 1], 4 * bi.dims[t], 1};
+          packpre.push_back(packtot);
+          packtot += (long long)bi.dims[t] * 4 * bi.dims[t + 1];
+          packs.push_back(pb);
+        }
+      }
+    }
+    // GEMM / MPO descriptors of every site of this wave
+    std::vector<TcGemmDesc> g1, g3;
+    std::vector<SpmmTDesc> sp;
+    std::vector<long long> g1pre, g3pre, sppre;
+    std::vector<int> g1n, g3n, spn;
+    for (int t = 0; t < N; ++t) {
+      long long tiles1 = 0, tiles3 = 0, tasks = 0;
+      for (int w = 0; w < nw; ++w) {
+        const int p = (int)p0 + w;
+        const DevMps& bi = *c->mps[pairs[p].first];
+        const KetView& kv = kets[p];
+        const int ca = bi.dims[t], ca2 = bi.dims[t + 1];
+        const int cb = kv.dims[t], cb2 = kv.dims[t + 1];
+        const int Din = bi.mpo.dims[t], Dout = bi.mpo.dims[t + 1];
+        float* Lin = (t & 1) ? env1[w] : env0[w];
+        float* Lout = (t & 1) ? env0[w] : env1[w];
+        TcGemmDesc d1;
+        std::memset(&d1, 0, sizeof(d1));
+        d1.M = ca * Din;
+        d1.N = 4 * cb2;
+        d1.K = cb;
+        encode_map(&d1.mapA, Lin, d1.M, cb, ld4(cb), TC_BM);
+        encode_map(&d1.mapB, ketT[w][t], d1.N, cb, ld4(cb), TC_BN);
+        d1.C = X[w];
+        d1.ldc = d1.N;
+        d1.cg = d1.N;
+        d1.cld = 0;
+        d1.tiles_n = (d1.N + TC_BN - 1) / TC_BN;
+        g1pre.push_back(tiles1);
+        tiles1 += (long long)((d1.M + TC_BM - 1) / TC_BM) * d1.tiles_n;
+        g1.push_back(d1);
+        SpmmTDesc s{};
+        s.rowptr = bi.d_rowptr[t];
+        s.col = bi.d_col[t];
+        s.val = bi.d_val32[t];
+        s.X = X[w];
+        s.Yt = Y[w];
+        s.chi_a = ca;
+        s.Din = Din;
+        s.Dout = Dout;
+        s.width = cb2;
+        s.ldy = 4 * ca;
+        sppre.push_back(tasks);
+        tasks += (long long)Dout * ((cb2 + 31) / 32) * ((ca + 31) / 32);
+        sp.push_back(s);
+        TcGemmDesc d3;
+        std::memset(&d3, 0, sizeof(d3));
+        d3.M = ca2;
+        d3.N = Dout * cb2;
+        d3.K = 4 * ca;
+        encode_map(&d3.mapA, braT[w][t], ca2, d3.K, d3.K, TC_BM);
+        encode_map(&d3.mapB, Y[w], d3.N, d3.K, d3.K, TC_BN);
+        d3.C = Lout;
+        d3.ldc = (long long)Dout * ld4(cb2);
+        d3.cg = cb2;
+        d3.cld = ld4(cb2);
+        d3.tiles_n = (d3.N + TC_BN - 1) / TC_BN;
+        g3pre.push_back(tiles3);
+        tiles3 += (long long)((d3.M + TC_BM - 1) / TC_BM) * d3.tiles_n;
+        g3.push_back(d3);
+      }
+      g1pre.push_back(tiles1);
+      g3pre.push_back(tiles3);
+      sppre.push_back(tasks);
+      g1n.push_back(nw);
+      g3n.push_back(nw);
+      spn.push_back(nw);
+    }
+    for (const TcGemmDesc& d : g1) c->prof[5] += 2.0 * d.M * d.N * d.K;
+    for (const TcGemmDesc& d : g3) c->prof[7] += 2.0 * d.M * d.N * d.K;
+    for (int w = 0; w < nw; ++w) {
+      const int p = (int)p0 + w;
+      const DevMps& bi = *c->mps[pairs[p].first];
+      const KetView& kv = kets[p];
+      for (int t = 0; t < N; ++t) {
+        const double ca = bi.dims[t], cb2 = kv.dims[t + 1];
+        c->prof[6] += 4.0 * ca * cb2 * 4.0 * (bi.mpo.dims[t] + bi.mpo.dims[t + 1]);
+        c->prof[8] += 2.0 * (double)bi.mpo.sites[t].val.size() * ca * cb2;
+      }
+    }
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    const size_t b1 = g1.size() * sizeof(TcGemmDesc), b3 = g3.size() * sizeof(TcGemmDesc);
+    const size_t bs = sp.size() * sizeof(SpmmTDesc), bpk = packs.size() * sizeof(PackDesc);
+    const size_t bp1 = g1pre.size() * 8, bp3 = g3pre.size() * 8, bps = sppre.size() * 8, bpp = (packpre.size() + 1) * 8;
+    const size_t bf = (size_t)nw * sizeof(float*);
+    const size_t o1 = 0, o3 = o1 + al(b1), os = o3 + al(b3), opk = os + al(bs), op1 = opk + al(bpk),
+                 op3 = op1 + al(bp1), ops = op3 + al(bp3), opp = ops + al(bps), of = opp + al(bpp);
+    const size_t total = of + al(bf);
+    std::vector<unsigned char> host(total, 0);
+    std::memcpy(host.data() + o1, g1.data(), b1);
+    std::memcpy(host.data() + o3, g3.data(), b3);
+    std::memcpy(host.data() + os, sp.data(), bs);
+    std::memcpy(host.data() + opk, packs.data(), bpk);
+    std::memcpy(host.data() + op1, g1pre.data(), bp1);
+    std::memcpy(host.data() + op3, g3pre.data(), bp3);
+    std::memcpy(host.data() + ops, sppre.data(), bps);
+    packpre.push_back(packtot);
+    std::memcpy(host.data() + opp, packpre.data(), bpp);
+    std::vector<const float*> fin(nw);
+    for (int w = 0; w < nw; ++w) fin[w] = (N & 1) ? env1[w] : env0[w];
+    std::memcpy(host.data() + of, fin.data(), bf);
+    c->tc_desc.ensure(total);
+    unsigned char* dd = c->tc_desc.as<unsigned char>();
+    CK(cudaMemcpyAsync(dd, host.data(), total, cudaMemcpyHostToDevice, c->stream));
+    {
+      const float one = 1.0f;
+      for (int w = 0; w < nw; ++w)
+        CK(cudaMemcpyAsync(env0[w], &one, sizeof(float), cudaMemcpyHostToDevice, c->stream));
+    }
+    CKL(launch_pack_sites(reinterpret_cast<PackDesc*>(dd + opk), reinterpret_cast<long long*>(dd + opp),
+                          (int)packs.size(), packtot, c->stream));
+    c->launches += 1;
+    int* derr = c->tc_err.as<int>();
+    size_t i1 = 0, i3 = 0, is = 0, ip1 = 0, ip3 = 0, ips = 0;
+    for (int t = 0; t < N; ++t) {
+      const int n1 = g1n[t], n3 = g3n[t], ns = spn[t];
+      cudaEvent_t* E = &c->pev[2 + 4 * t];
+      CK(cudaEventRecord(E[0], c->stream));
+      CKL(launch_gemm_tf32x3(reinterpret_cast<TcGemmDesc*>(dd + o1) + i1, reinterpret_cast<long long*>(dd + op1) + ip1,
+                             n1, g1pre[ip1 + n1], c->opt.max_spin, derr, c->stream));
+      CK(cudaEventRecord(E[1], c->stream));
+      CKL(launch_spmm_t_f32(reinterpret_cast<SpmmTDesc*>(dd + os) + is, reinterpret_cast<long long*>(dd + ops) + ips,
+                            ns, sppre[ips + ns], c->stream));
+      CK(cudaEventRecord(E[2], c->stream));
+      CKL(launch_gemm_tf32x3(reinterpret_cast<TcGemmDesc*>(dd + o3) + i3, reinterpret_cast<long long*>(dd + op3) + ip3,
+                             n3, g3pre[ip3 + n3], c->opt.max_spin, derr, c->stream));
+      CK(cudaEventRecord(E[3], c->stream));
+      c->launches += 3;
+      i1 += n1;
+      i3 += n3;
+      is += ns;
+      ip1 += n1 + 1;
+      ip3 += n3 + 1;
+      ips += ns + 1;
+    }
+    CKL(launch_extract_f32(reinterpret_cast<const float* const*>(dd + of), nw, 4, d_H + p0, d_S + p0, c->stream));
+    c->launches += 1;
+    CK(cudaStreamSynchronize(c->stream));
+    for (int t = 0; t < N; ++t) {
+      cudaEvent_t* E = &c->pev[2 + 4 * t];
+      float a = 0.f, b = 0.f, d = 0.f;
+      CK(cudaEventElapsedTime(&a, E[0], E[1]));
+      CK(cudaEventElapsedTime(&b, E[1], E[2]));
+      CK(cudaEventElapsedTime(&d, E[2], E[3]));
+      c->prof[1] += a;
+      c->prof[2] += b;
+      c->prof[3] += d;
+    }
+    p0 = p1;
+  }
+  int herr = 0;
+  CK(cudaMemcpy(&herr, c->tc_err.p, sizeof(int), cudaMemcpyDeviceToHost));
+  if (herr) throw Error(TNQE_ERR_TIMEOUT, "a tensor-core pipeline wait ran out of iterations");
+}
+
 void check_ctx(tnqe_ctx* c) {
   if (!c) throw Error(TNQE_ERR_ARG, "null context");
   CK(cudaSetDevice(c->opt.device));
@@ -661,6 +924,8 @@ void prepare_mps(tnqe_ctx* c, const double* const* tensors, const int* bond_dims
     m.d_rowptr.push_back(dalloc_copy(m.mpo.sites[t].rowptr, m.owned));
     m.d_col.push_back(dalloc_copy(m.mpo.sites[t].col, m.owned));
     m.d_val.push_back(dalloc_copy(m.mpo.sites[t].val, m.owned));
+    std::vector<float> v32(m.mpo.sites[t].val.begin(), m.mpo.sites[t].val.end());
+    m.d_val32.push_back(dalloc_copy(v32, m.owned));
   }
 }
 
@@ -838,8 +1103,8 @@ tnqe_status tnqe_matrix_elements(tnqe_ctx* c, const int* pairs, int npairs, doub
       if (i > j) throw Error(TNQE_ERR_ARG, "pairs must have i <= j");
       pl[p] = {i, j};
     }
-    if (c->opt.precision != TNQE_PREC_FP64)
-      throw Error(TNQE_ERR_ARG, "this build supports the FP64 contraction only");
+    if (c->opt.precision == TNQE_PREC_BF16X3)
+      throw Error(TNQE_ERR_ARG, "the BF16x3 contraction is not built; use TNQE_PREC_FP64 or TNQE_PREC_TF32X3");
     c->launches = 0;
     c->kept_pair_valid = 0;
     for (double& x : c->prof) x = 0.0;
@@ -870,7 +1135,8 @@ tnqe_status tnqe_matrix_elements(tnqe_ctx* c, const int* pairs, int npairs, doub
     c->con_out.ensure(sizeof(double) * 2 * npairs);
     double* dH = c->con_out.as<double>();
     double* dS = dH + npairs;
-    run_contractions(c, pl, kets, dH, dS);
+    if (c->opt.precision == TNQE_PREC_TF32X3) run_contractions_tc(c, pl, kets, dH, dS);
+    else run_contractions(c, pl, kets, dH, dS);
     CK(cudaEventRecord(c->ev[3], c->stream));
     const bool hdev = is_device_ptr(H_out), sdev = is_device_ptr(S_out);
     CK(cudaMemcpyAsync(H_out, dH, sizeof(double) * npairs, hdev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
@@ -972,6 +1238,9 @@ void tnqe_destroy(tnqe_ctx* c) {
   c->con_ws.release();
   c->con_desc.release();
   c->con_out.release();
+  c->tc_ws.release();
+  c->tc_desc.release();
+  c->tc_err.release();
   for (auto& e : c->ev)
     if (e) cudaEventDestroy(e);
   for (auto& e : c->pev)

@@ -70,9 +70,13 @@ struct RotDesc {
   const double* gates;            // ngates * 256
   const int* gate_site;
   const int* gate_side;
-  double* theta;                  // scratch
-  double* wbuf;
-  double* qbuf;
+  double* theta;                  // scratch: two-site tensor
+  double* bbuf;                   // SVD blocks (scaled copies of the gated two-site blocks)
+  double* wbuf;                   // B V per block
+  double* qbuf;                   // V per block
+  double* tbuf;                   // n x n temporaries per block
+  float* w32;                     // FP32 working copy of each block
+  float* q32;                     // FP32 rotations of each block
   int* meta;                      // scratch ints
   long long meta_cap;
   double* discarded;
@@ -97,6 +101,22 @@ struct SpmmDesc {                 // Y[a][row][:] = sum val * X[a][col][:], rows
   double* Y;                      // [a][4][Dout][width] == [a][nrows][width]
 };
 
+// split-precision contraction (kernels_tc.cu)
+struct PackDesc {                 // mode 0: ketT[(k',b')][b] = B[b][k'][b'];  mode 1: braT[a'][(a,k)] = A[a][k][a']
+  const double* src;
+  float* dst;
+  int cl, cr, ld, mode;
+};
+struct SpmmTDesc {                // Yt[(w',b')][(a,k)] = sum W[(w',k),(w,k')] X[(a,w)][(k',b')]
+  const int* rowptr;
+  const int* col;
+  const float* val;
+  const float* X;
+  float* Yt;
+  int chi_a, Din, Dout, width, ldy, pad;
+};
+struct TcGemmDesc;
+
 // status bits written by kernels
 constexpr int STATUS_NOCONV = 1;
 constexpr int STATUS_OVERFLOW = 2;
@@ -108,6 +128,11 @@ int launch_gemm_f64(const GemmDesc* d_descs, const long long* d_tile_prefix, int
 int launch_spmm_f64(const SpmmDesc* d_descs, const long long* d_row_prefix, int nprob,
                     long long total_rows, void* stream);
 int launch_extract(const double* const* d_final, int npairs, double* H, double* S, void* stream);
+int launch_pack_sites(const PackDesc* d, const long long* prefix, int n, long long total, void* stream);
+int launch_gemm_tf32x3(const TcGemmDesc* d, const long long* tile_prefix, int nprob, long long total_tiles,
+                       long long max_spin, int* err, void* stream);
+int launch_spmm_t_f32(const SpmmTDesc* d, const long long* prefix, int nprob, long long total, void* stream);
+int launch_extract_f32(const float* const* fin, int npairs, int ld, double* H, double* S, void* stream);
 int launch_solve(const double* d_H, const double* d_S, int M, double eps, int max_sweeps,
                  double* d_E, double* d_C, int* d_rank, double* d_kappa, int* d_status, void* stream);
 

@@ -120,9 +120,193 @@ __device__ int jacobi_block(double* W, double* Q, int m, int n, int max_sweeps, 
   return noconv;
 }
 
-__global__ void __launch_bounds__(ROT_THREADS) rotate_pairs_kernel(const RotDesc* __restrict__ descs) {
+constexpr int RT_THREADS = 512;
+constexpr int RT_WARPS = RT_THREADS / 32;
+constexpr int MAXBLK = 1024;
+
+__device__ __forceinline__ float grp8_sum(float v, unsigned mask) {
+  v += __shfl_xor_sync(mask, v, 4);
+  v += __shfl_xor_sync(mask, v, 2);
+  v += __shfl_xor_sync(mask, v, 1);
+  return v;
+}
+__device__ __forceinline__ double grp8_sum(double v, unsigned mask) {
+  v += __shfl_xor_sync(mask, v, 4);
+  v += __shfl_xor_sync(mask, v, 2);
+  v += __shfl_xor_sync(mask, v, 1);
+  return v;
+}
+
+// 2^-e for the binary exponent e of a positive normal double (integer ops only)
+__device__ __forceinline__ double exp2_neg_exponent(double x) {
+  const int ex = ((__double2hiint(x) >> 20) & 0x7ff) - 1023;
+  return __hiloint2double((1023 - ex) << 20, 0);
+}
+
+// SVD of one block by one warp, mixed precision.  Bm (m x n column-major,
+// n <= m, scaled to max |entry| = 1) is left untouched; on return
+// W = Bm Q with mutually orthogonal columns (FP64) and Q (n x n) orthogonal
+// to FP64 precision.  Steps: FP32 one-sided Jacobi on a copy of Bm until the
+// columns are orthogonal at FP32 level; Q = Newton-Schulz orthogonalisation
+// of the FP32 rotations in FP64; W = Bm Q in FP64; FP64 one-sided Jacobi
+// sweeps from that nearly orthogonal start (rotation angles computed in FP32,
+// cos/sin normalised in FP64 so every rotation is orthogonal in FP64).
+// Column pairs of a tournament round go to the four 8-lane groups of the warp.
+// Returns 1 if a phase hit the sweep limit.
+__device__ int block_svd_warp(const double* __restrict__ Bm, double* __restrict__ W, double* __restrict__ Q,
+                              float* __restrict__ W32, float* __restrict__ Q32, double* __restrict__ T, int m,
+                              int n, int max_sweeps) {
+  const int lane = threadIdx.x & 31, grp = lane >> 3, gl = lane & 7;
+  const unsigned gmask = 0xffu << (grp * 8);
+  const int n2 = n + (n & 1);
+  int noconv = 0;
+  // ---- FP32 phase
+  for (int idx = lane; idx < m * n; idx += 32) W32[idx] = (float)Bm[idx];
+  for (int idx = lane; idx < n * n; idx += 32) Q32[idx] = (idx / n == idx % n) ? 1.f : 0.f;
+  __syncwarp();
+  if (n >= 2) {
+    const float tol32 = 1.2e-7f * (float)m;
+    int done = 0;
+    for (int sweep = 0; sweep < max_sweeps && !done; ++sweep) {
+      int rot = 0;
+      for (int r = 0; r < n2 - 1; ++r) {
+        for (int k = grp; k < n2 / 2; k += 4) {
+          int i, j;
+          tour_pair(r, k, n2, i, j);
+          if (i >= n || j >= n) continue;
+          float* x = W32 + (size_t)i * m;
+          float* y = W32 + (size_t)j * m;
+          float al = 0.f, be = 0.f, ga = 0.f;
+          for (int t = gl; t < m; t += 8) {
+            const float xv = x[t], yv = y[t];
+            al = fmaf(xv, xv, al);
+            be = fmaf(yv, yv, be);
+            ga = fmaf(xv, yv, ga);
+          }
+          al = grp8_sum(al, gmask);
+          be = grp8_sum(be, gmask);
+          ga = grp8_sum(ga, gmask);
+          if (ga == 0.f || al < 1e-30f || be < 1e-30f || !(fabsf(ga) > tol32 * sqrtf(al) * sqrtf(be))) continue;
+          const float zeta = (be - al) / (2.f * ga);
+          const float t = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + hypotf(1.f, zeta));
+          const float c = rsqrtf(1.f + t * t), s = c * t;
+          if (s == 0.f) continue;
+          for (int u = gl; u < m; u += 8) {
+            const float xv = x[u], yv = y[u];
+            x[u] = c * xv - s * yv;
+            y[u] = s * xv + c * yv;
+          }
+          float* qx = Q32 + (size_t)i * n;
+          float* qy = Q32 + (size_t)j * n;
+          for (int u = gl; u < n; u += 8) {
+            const float xv = qx[u], yv = qy[u];
+            qx[u] = c * xv - s * yv;
+            qy[u] = s * xv + c * yv;
+          }
+          rot = 1;
+        }
+        __syncwarp();
+      }
+      done = !__any_sync(0xffffffffu, rot);
+    }
+  }
+  // ---- Q = orthogonalised FP32 rotations: Newton-Schulz Q <- Q (1.5 I - 0.5 Q^T Q) in FP64,
+  // twice: the FP32 product is orthogonal to ~1e-6, each step squares the defect
+  for (int idx = lane; idx < n * n; idx += 32) Q[idx] = (double)Q32[idx];
+  __syncwarp();
+  for (int it = 0; it < 2; ++it) {
+    for (int idx = lane; idx < n * n; idx += 32) {
+      const int i = idx % n, j = idx / n;
+      const double* qi = Q + (size_t)i * n;
+      const double* qj = Q + (size_t)j * n;
+      double acc = 0.0;
+      for (int k = 0; k < n; ++k) acc = fma(qi[k], qj[k], acc);
+      T[idx] = (i == j ? 1.5 : 0.0) - 0.5 * acc;
+    }
+    __syncwarp();
+    for (int idx = lane; idx < n * n; idx += 32) {
+      const int row = idx % n, col = idx / n;
+      double acc = 0.0;
+      for (int k = 0; k < n; ++k) acc = fma(Q[(size_t)k * n + row], T[(size_t)col * n + k], acc);
+      W[idx] = acc;                                // W used as temporary (m*n >= n*n)
+    }
+    __syncwarp();
+    for (int idx = lane; idx < n * n; idx += 32) Q[idx] = W[idx];
+    __syncwarp();
+  }
+  // ---- W = Bm Q
+  for (int idx = lane; idx < m * n; idx += 32) {
+    const int row = idx % m, col = idx / m;
+    const double* qc = Q + (size_t)col * n;
+    double acc = 0.0;
+    for (int k = 0; k < n; ++k) acc = fma(Bm[(size_t)k * m + row], qc[k], acc);
+    W[idx] = acc;
+  }
+  __syncwarp();
+  if (n < 2) return noconv;
+  // ---- FP64 phase
+  const double tol64 = 2.220446049250313e-16 * (double)m;
+  const float tol64sq = (float)(tol64 * tol64);
+  noconv = 1;
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    int rot = 0;
+    for (int r = 0; r < n2 - 1; ++r) {
+      for (int k = grp; k < n2 / 2; k += 4) {
+        int i, j;
+        tour_pair(r, k, n2, i, j);
+        if (i >= n || j >= n) continue;
+        double* x = W + (size_t)i * m;
+        double* y = W + (size_t)j * m;
+        double al = 0.0, be = 0.0, ga = 0.0;
+        for (int t = gl; t < m; t += 8) {
+          const double xv = x[t], yv = y[t];
+          al = fma(xv, xv, al);
+          be = fma(yv, yv, be);
+          ga = fma(xv, yv, ga);
+        }
+        al = grp8_sum(al, gmask);
+        be = grp8_sum(be, gmask);
+        ga = grp8_sum(ga, gmask);
+        // columns below 1e-125 of the block's largest entry are zero at this precision
+        if (ga == 0.0 || al < 1e-250 || be < 1e-250) continue;
+        const double sc = exp2_neg_exponent(fmax(al, be));
+        const float af = (float)(al * sc), bf = (float)(be * sc), gf = (float)(ga * sc);
+        if (!(gf * gf > tol64sq * af * bf)) continue;
+        const float zeta = (bf - af) / (2.f * gf);
+        const float t32 = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + hypotf(1.f, zeta));
+        const double t = (double)t32, w = fma(t, t, 1.0);
+        double c = (double)rsqrtf((float)w);
+        c = c * fma(-0.5 * w, c * c, 1.5);
+        c = c * fma(-0.5 * w, c * c, 1.5);
+        const double s = t * c;
+        if (s == 0.0) continue;
+        for (int u = gl; u < m; u += 8) {
+          const double xv = x[u], yv = y[u];
+          x[u] = c * xv - s * yv;
+          y[u] = s * xv + c * yv;
+        }
+        double* qx = Q + (size_t)i * n;
+        double* qy = Q + (size_t)j * n;
+        for (int u = gl; u < n; u += 8) {
+          const double xv = qx[u], yv = qy[u];
+          qx[u] = c * xv - s * yv;
+          qy[u] = s * xv + c * yv;
+        }
+        rot = 1;
+      }
+      __syncwarp();
+    }
+    if (!__any_sync(0xffffffffu, rot)) {
+      noconv = 0;
+      break;
+    }
+  }
+  return noconv;
+}
+
+__global__ void __launch_bounds__(RT_THREADS) rotate_pairs_kernel(const RotDesc* __restrict__ descs) {
   const RotDesc& D = descs[blockIdx.x];
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int N = D.N;
 
   __shared__ int lutL[QSPACE], lutM[QSPACE], lutR[QSPACE];
@@ -131,24 +315,25 @@ __global__ void __launch_bounds__(ROT_THREADS) rotate_pairs_kernel(const RotDesc
   __shared__ int gnz_n[16], gnz_k[16][16];
   __shared__ double gnz_v[16][16];
   __shared__ double sig[MAXSIG];
-  __shared__ short sig_blk[MAXSIG], sig_col[MAXSIG];
   __shared__ unsigned char sig_keep[MAXSIG];
-  __shared__ int s_nblk, s_nnew, s_total, s_nsig, s_keep, s_flag, s_status;
-  __shared__ double s_disc, s_smax, s_red[ROT_WARPS], s_flops;
+  __shared__ short s_ord[MAXBLK];
+  __shared__ int s_nblk, s_nnew, s_total, s_nsig, s_keep, s_status;
+  __shared__ double s_disc, s_red[RT_WARPS], s_flops;
 
   ThetaBlk* tb = reinterpret_cast<ThetaBlk*>(D.meta);
   const long long tb_cap = D.meta_cap / 2 / (long long)(sizeof(ThetaBlk) / sizeof(int));
   NewBlk* nb = reinterpret_cast<NewBlk*>(D.meta + D.meta_cap / 2);
-  const long long nb_cap = D.meta_cap / 2 / (long long)(sizeof(NewBlk) / sizeof(int));
+  long long nb_cap = D.meta_cap / 2 / (long long)(sizeof(NewBlk) / sizeof(int));
+  if (nb_cap > MAXBLK) nb_cap = MAXBLK;
 
   // ---- copy the input state into the work buffer
   for (int s = 0; s < N; ++s) {
     const long long n = (long long)D.src_dims[s] * 4 * D.src_dims[s + 1];
     const double* src = D.src + D.src_off[s];
     double* dst = D.work + D.work_off[s];
-    for (long long x = tid; x < n; x += ROT_THREADS) dst[x] = src[x];
+    for (long long x = tid; x < n; x += RT_THREADS) dst[x] = src[x];
   }
-  for (int b = tid; b <= N; b += ROT_THREADS) {
+  for (int b = tid; b <= N; b += RT_THREADS) {
     D.work_dims[b] = D.src_dims[b];
     D.work_sec[b] = D.src_sec[b];
   }
@@ -162,21 +347,27 @@ __global__ void __launch_bounds__(ROT_THREADS) rotate_pairs_kernel(const RotDesc
   for (int g = 0; g < D.ngates; ++g) {
     const int a = D.gate_site[g];
     const int side = D.gate_side[g];
-    for (int x = tid; x < QSPACE; x += ROT_THREADS) {
+    for (int x = tid; x < QSPACE; x += RT_THREADS) {
       lutL[x] = -1;
       lutM[x] = -1;
       lutR[x] = -1;
     }
-    if (tid == 0) {
-      secL = D.work_sec[a];
-      secM = D.work_sec[a + 1];
-      secR = D.work_sec[a + 2];
+    {
+      constexpr int W4 = (int)(sizeof(SectorTable) / 4);
+      const int* srcs = reinterpret_cast<const int*>(D.work_sec + a);
+      int* dL = reinterpret_cast<int*>(&secL);
+      int* dM = reinterpret_cast<int*>(&secM);
+      int* dR = reinterpret_cast<int*>(&secR);
+      for (int x = tid; x < 3 * W4; x += RT_THREADS) {
+        const int v = srcs[x];
+        if (x < W4) dL[x] = v; else if (x < 2 * W4) dM[x - W4] = v; else dR[x - 2 * W4] = v;
+      }
     }
-    for (int x = tid; x < 256; x += ROT_THREADS) G[x] = D.gates[(size_t)g * 256 + x];
+    for (int x = tid; x < 256; x += RT_THREADS) G[x] = D.gates[(size_t)g * 256 + x];
     __syncthreads();
-    for (int x = tid; x < secL.nsec; x += ROT_THREADS) lutL[secL.q[x]] = x;
-    for (int x = tid; x < secM.nsec; x += ROT_THREADS) lutM[secM.q[x]] = x;
-    for (int x = tid; x < secR.nsec; x += ROT_THREADS) lutR[secR.q[x]] = x;
+    for (int x = tid; x < secL.nsec; x += RT_THREADS) lutL[secL.q[x]] = x;
+    for (int x = tid; x < secM.nsec; x += RT_THREADS) lutM[secM.q[x]] = x;
+    for (int x = tid; x < secR.nsec; x += RT_THREADS) lutR[secR.q[x]] = x;
     if (tid < 16) {                       // nonzero inputs of each gate row
       int c = 0;
       for (int K = 0; K < 16; ++K) {
@@ -222,7 +413,7 @@ __global__ void __launch_bounds__(ROT_THREADS) rotate_pairs_kernel(const RotDesc
     __syncthreads();
     {
       const int nblk = s_nblk, total = s_total;
-      for (int idx = tid; idx < total; idx += ROT_THREADS) {
+      for (int idx = tid; idx < total; idx += RT_THREADS) {
         int lo = 0, hi = nblk - 1;
         while (lo < hi) {
           const int mid = (lo + hi + 1) >> 1;
@@ -269,6 +460,7 @@ __global__ void __launch_bounds__(ROT_THREADS) rotate_pairs_kernel(const RotDesc
         B.sofs = nsig;
         B.kept = 0;
         B.newoff = 0;
+        B.scale = 1.0;
         wofs += (long long)mm * nn;
         qofs += (long long)nn * nn;
         s_flops += 4.0 * mm * nn * nn + 8.0 * nn * nn * nn + 8.0 * mm * nn;
@@ -286,14 +478,33 @@ __global__ void __launch_bounds__(ROT_THREADS) rotate_pairs_kernel(const RotDesc
     }
     __syncthreads();
     const int nnew = s_nnew;
-    // ---- SVD of every block
-    for (int b = 0; b < nnew; ++b) {
+    // ---- largest blocks first: rank by m n^2
+    for (int b = tid; b < nnew; b += RT_THREADS) {
+      const NewBlk& B = nb[b];
+      const long long cb = (long long)(B.nr > B.nc ? B.nr : B.nc) * (B.nr < B.nc ? B.nr : B.nc) * (B.nr < B.nc ? B.nr : B.nc);
+      int rank = 0;
+      for (int b2 = 0; b2 < nnew; ++b2) {
+        const NewBlk& C = nb[b2];
+        const long long cc = (long long)(C.nr > C.nc ? C.nr : C.nc) * (C.nr < C.nc ? C.nr : C.nc) * (C.nr < C.nc ? C.nr : C.nc);
+        rank += (cc > cb || (cc == cb && b2 < b)) ? 1 : 0;
+      }
+      s_ord[rank] = (short)b;
+    }
+    __syncthreads();
+    // ---- SVD of every block, one warp per block
+    for (int bi = warp; bi < nnew; bi += RT_WARPS) {
+      const int b = s_ord[bi];
       const NewBlk B = nb[b];
       const bool trans = B.nc > B.nr;                // work on B^T so that n <= m
       const int m = trans ? B.nc : B.nr, n = trans ? B.nr : B.nc;
+      double* Bm = D.bbuf + B.wofs;
       double* W = D.wbuf + B.wofs;
+      float* W32 = D.w32 + B.wofs;
       double* Q = D.qbuf + B.qofs;
-      for (int idx = tid; idx < m * n; idx += ROT_THREADS) {
+      double* T = D.tbuf + B.qofs;
+      float* Q32 = D.q32 + B.qofs;
+      double mx = 0.0;
+      for (int idx = lane; idx < m * n; idx += 32) {
         const int wi = idx % m, wj = idx / m;
         const int br = trans ? wj : wi, bc = trans ? wi : wj;
         int k1p = 3, k2p = 3;
@@ -311,46 +522,30 @@ __global__ void __launch_bounds__(ROT_THREADS) rotate_pairs_kernel(const RotDesc
           if (qM < 0 || lutM[qM] < 0) continue;       // that theta block is zero
           acc = fma(gnz_v[Kp][e], D.theta[(((size_t)l * 4 + k1) * 4 + k2) * chr + r], acc);
         }
-        W[idx] = acc;
+        Bm[idx] = acc;
+        mx = fmax(mx, fabs(acc));
       }
-      __syncthreads();
-      {
-        double mx = 0.0;
-        for (int idx = tid; idx < m * n; idx += ROT_THREADS) mx = fmax(mx, fabs(W[idx]));
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        if ((tid & 31) == 0) s_red[tid >> 5] = mx;
-        __syncthreads();
-        double bmax = 0.0;
-        for (int w = 0; w < ROT_WARPS; ++w) bmax = fmax(bmax, s_red[w]);
-        const double scale = bmax > 0.0 ? bmax : 1.0;
-        const double inv = 1.0 / scale;
-        for (int idx = tid; idx < m * n; idx += ROT_THREADS) W[idx] *= inv;
-        if (tid == 0) nb[b].scale = scale;
-        __syncthreads();
-      }
-      const int nc_flag = jacobi_block(W, Q, m, n, D.max_sweeps, &s_flag);
-      if (nc_flag && tid == 0) s_status |= STATUS_NOCONV | (min(m, 4095) << 8) | (min(n, 4095) << 20);
-      // singular values = column norms
+      for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      const double scale = mx > 0.0 ? mx : 1.0;
+      const double inv = 1.0 / scale;
+      __syncwarp();
+      for (int idx = lane; idx < m * n; idx += 32) Bm[idx] *= inv;
+      if (lane == 0) nb[b].scale = scale;
+      __syncwarp();
+      const int ncv = block_svd_warp(Bm, W, Q, W32, Q32, T, m, n, D.max_sweeps);
+      if (ncv && lane == 0) atomicOr(&s_status, STATUS_NOCONV | (min(m, 4095) << 8) | (min(n, 4095) << 20));
       for (int j = 0; j < n; ++j) {
         double acc = 0.0;
-        for (int u = tid; u < m; u += ROT_THREADS) {
+        for (int u = lane; u < m; u += 32) {
           const double v = W[(size_t)j * m + u];
           acc = fma(v, v, acc);
         }
         acc = warp_sum(acc);
-        if ((tid & 31) == 0) s_red[tid >> 5] = acc;
-        __syncthreads();
-        if (tid == 0) {
-          double t = 0.0;
-          for (int w = 0; w < ROT_WARPS; ++w) t += s_red[w];
-          sig[B.sofs + j] = sqrt(t) * nb[b].scale;
-          sig_blk[B.sofs + j] = (short)b;
-          sig_col[B.sofs + j] = (short)j;
-        }
-        __syncthreads();
+        if (lane == 0) sig[B.sofs + j] = sqrt(acc) * scale;
       }
     }
+    __syncthreads();
     // ---- global truncation: k = min(chi_rot, #{sigma > cutoff sigma_1}), at least 1
     const int nsig = s_nsig;
     if (tid == 0) {
@@ -363,10 +558,9 @@ __global__ void __launch_bounds__(ROT_THREADS) rotate_pairs_kernel(const RotDesc
       if (keep < 1) keep = 1;
       if (keep > nsig) keep = nsig;
       s_keep = keep;
-      s_smax = smax;
     }
     __syncthreads();
-    for (int x = tid; x < nsig; x += ROT_THREADS) {
+    for (int x = tid; x < nsig; x += RT_THREADS) {
       const double v = sig[x];
       int rank = 0;
       for (int y = 0; y < nsig; ++y) rank += (sig[y] > v || (sig[y] == v && y < x)) ? 1 : 0;
@@ -394,16 +588,21 @@ __global__ void __launch_bounds__(ROT_THREADS) rotate_pairs_kernel(const RotDesc
         }
         off += kept;
       }
-      D.work_sec[a + 1] = nt;
       D.work_dims[a + 1] = off;
     }
     __syncthreads();
+    {
+      constexpr int W4 = (int)(sizeof(SectorTable) / 4);
+      const int* srcp = reinterpret_cast<const int*>(&secM);
+      int* dst = reinterpret_cast<int*>(D.work_sec + a + 1);
+      for (int x = tid; x < W4; x += RT_THREADS) dst[x] = srcp[x];
+    }
     // ---- write the two new site tensors
     const int knew = D.work_dims[a + 1];
-    for (long long x = tid; x < (long long)chl * 4 * knew; x += ROT_THREADS) Lt[x] = 0.0;
-    for (long long x = tid; x < (long long)knew * 4 * chr; x += ROT_THREADS) Rt[x] = 0.0;
+    for (long long x = tid; x < (long long)chl * 4 * knew; x += RT_THREADS) Lt[x] = 0.0;
+    for (long long x = tid; x < (long long)knew * 4 * chr; x += RT_THREADS) Rt[x] = 0.0;
     __syncthreads();
-    for (int b = 0; b < nnew; ++b) {
+    for (int b = warp; b < nnew; b += RT_WARPS) {
       const NewBlk B = nb[b];
       if (B.kept == 0) continue;
       const bool trans = B.nc > B.nr;
@@ -417,7 +616,7 @@ __global__ void __launch_bounds__(ROT_THREADS) rotate_pairs_kernel(const RotDesc
         const double sj = sig[B.sofs + j];
         const double inv = sj > 0.0 ? 1.0 / sj : 0.0;
         // left factor column over block rows (l, k1'), right factor row over block cols (k2', r)
-        for (int br = tid; br < B.nr; br += ROT_THREADS) {
+        for (int br = lane; br < B.nr; br += 32) {
           int k1p = 3;
           while (k1p > 0 && (B.rowsec[k1p] < 0 || B.rowoff[k1p] > br)) --k1p;
           const int l = secL.off[B.rowsec[k1p]] + (br - B.rowoff[k1p]);
@@ -426,7 +625,7 @@ __global__ void __launch_bounds__(ROT_THREADS) rotate_pairs_kernel(const RotDesc
           else v = (side == 0) ? Q[(size_t)j * n + br] * sj : Q[(size_t)j * n + br];
           Lt[((size_t)l * 4 + k1p) * knew + newidx] = v;
         }
-        for (int bc = tid; bc < B.nc; bc += ROT_THREADS) {
+        for (int bc = lane; bc < B.nc; bc += 32) {
           int k2p = 3;
           while (k2p > 0 && (B.colsec[k2p] < 0 || B.coloff[k2p] > bc)) --k2p;
           const int r = secR.off[B.colsec[k2p]] + (bc - B.coloff[k2p]);
@@ -446,7 +645,7 @@ __global__ void __launch_bounds__(ROT_THREADS) rotate_pairs_kernel(const RotDesc
     const int s = D.neg_site;
     double* T = D.work + D.work_off[s];
     const int cl = D.work_dims[s], cr = D.work_dims[s + 1];
-    for (long long x = tid; x < (long long)cl * 4 * cr; x += ROT_THREADS) {
+    for (long long x = tid; x < (long long)cl * 4 * cr; x += RT_THREADS) {
       const int k = (int)((x / cr) % 4);
       if (k == 1 || k == 2) T[x] = -T[x];
     }
@@ -461,23 +660,23 @@ __global__ void __launch_bounds__(ROT_THREADS) rotate_pairs_kernel(const RotDesc
     const double* S0 = D.src + D.src_off[N - 1];
     const long long n0 = (long long)D.src_dims[N - 1] * 4;
     double a1 = 0.0, a0 = 0.0;
-    for (long long x = tid; x < n; x += ROT_THREADS) a1 = fma(T[x], T[x], a1);
-    for (long long x = tid; x < n0; x += ROT_THREADS) a0 = fma(S0[x], S0[x], a0);
+    for (long long x = tid; x < n; x += RT_THREADS) a1 = fma(T[x], T[x], a1);
+    for (long long x = tid; x < n0; x += RT_THREADS) a0 = fma(S0[x], S0[x], a0);
     a1 = warp_sum(a1);
     a0 = warp_sum(a0);
-    __shared__ double r1[ROT_WARPS], r0[ROT_WARPS];
-    if ((tid & 31) == 0) {
-      r1[tid >> 5] = a1;
-      r0[tid >> 5] = a0;
+    __shared__ double r1[RT_WARPS], r0[RT_WARPS];
+    if (lane == 0) {
+      r1[warp] = a1;
+      r0[warp] = a0;
     }
     __syncthreads();
     double t1 = 0.0, t0 = 0.0;
-    for (int w = 0; w < ROT_WARPS; ++w) {
+    for (int w = 0; w < RT_WARPS; ++w) {
       t1 += r1[w];
       t0 += r0[w];
     }
     const double f = t1 > 0.0 ? sqrt(t0 / t1) : 1.0;
-    for (long long x = tid; x < n; x += ROT_THREADS) T[x] *= f;
+    for (long long x = tid; x < n; x += RT_THREADS) T[x] *= f;
   }
   if (tid == 0) {
     *D.discarded = s_disc;
@@ -491,7 +690,7 @@ __global__ void __launch_bounds__(ROT_THREADS) rotate_pairs_kernel(const RotDesc
 int launch_rotate(const RotDesc* d_descs, int npairs, int smem_bytes, void* stream) {
   if (npairs <= 0) return 0;
   (void)smem_bytes;
-  rotate_pairs_kernel<<<npairs, ROT_THREADS, 0, (cudaStream_t)stream>>>(d_descs);
+  rotate_pairs_kernel<<<npairs, RT_THREADS, 0, (cudaStream_t)stream>>>(d_descs);
   return (int)cudaGetLastError();
 }
 

@@ -272,3 +272,26 @@ def test_n14_mixed_sampled_pairs():
     for i in range(w.M):
         assert abs(SG[allp.index((i, i))] - 1.0) <= 1e-12
     assert np.all(np.isfinite(HG)) and np.all(np.isfinite(SG))
+
+
+# ----------------------------------------------------------------------------- split precision
+def test_tf32x3_contraction_error_against_fp64():
+    """TF32x3 tensor-core contraction: errors stated as numbers against the FP64 path.
+
+    Bounds (measured 1.9e-4 / 3.1e-6 / 1.5e-5 on this workload): FP32
+    accumulation limits H_ii ~ 56 Ha to ~1e-5 relative.
+    """
+    w = inputs.workload("n10_chi32")
+    pairs = w.all_pairs()
+    out = {}
+    for prec in (0, 1):
+        with gpu_ctx(w, precision=prec) as g:
+            Hv, Sv = g.matrix_elements(pairs)
+            E = g.solve(*assemble(w.M, pairs, Hv, Sv))[0]
+        out[prec] = (Hv, Sv, E)
+    (H0, S0, E0), (H1, S1, E1) = out[0], out[1]
+    assert np.abs(H1 - H0).max() <= 1e-5 * np.abs(H0).max()
+    assert np.abs(S1 - S0).max() <= 2e-5
+    assert abs(E1[0] - E0[0]) <= 1e-4
+    off = [k for k, (i, j) in enumerate(pairs) if i != j]
+    assert np.abs(H1[off] - H0[off]).max() <= 1e-5
