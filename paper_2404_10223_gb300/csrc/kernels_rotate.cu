@@ -123,6 +123,7 @@ __device__ int jacobi_block(double* W, double* Q, int m, int n, int max_sweeps, 
 constexpr int RT_THREADS = 512;
 constexpr int RT_WARPS = RT_THREADS / 32;
 constexpr int MAXBLK = 1024;
+constexpr int BIG_BLOCK_N = 24;    // blocks with min(rows, cols) >= this use the whole CTA
 
 __device__ __forceinline__ float grp8_sum(float v, unsigned mask) {
   v += __shfl_xor_sync(mask, v, 4);
@@ -143,34 +144,66 @@ __device__ __forceinline__ double exp2_neg_exponent(double x) {
   return __hiloint2double((1023 - ex) << 20, 0);
 }
 
-// SVD of one block by one warp, mixed precision.  Bm (m x n column-major,
-// n <= m, scaled to max |entry| = 1) is left untouched; on return
-// W = Bm Q with mutually orthogonal columns (FP64) and Q (n x n) orthogonal
-// to FP64 precision.  Steps: FP32 one-sided Jacobi on a copy of Bm until the
-// columns are orthogonal at FP32 level; Q = Newton-Schulz orthogonalisation
-// of the FP32 rotations in FP64; W = Bm Q in FP64; FP64 one-sided Jacobi
-// sweeps from that nearly orthogonal start (rotation angles computed in FP32,
-// cos/sin normalised in FP64 so every rotation is orthogonal in FP64).
-// Column pairs of a tournament round go to the four 8-lane groups of the warp.
+// A team of threads that works on one SVD block: a single warp, or the whole CTA.
+struct WarpTeam {
+  __device__ static int rank() { return threadIdx.x & 31; }
+  __device__ static int size() { return 32; }
+  __device__ static void sync() { __syncwarp(); }
+  __device__ static int any(int v) { return __any_sync(0xffffffffu, v); }
+  __device__ static float max(float v, float* /*scratch*/) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+  }
+};
+struct CtaTeam {
+  __device__ static int rank() { return threadIdx.x; }
+  __device__ static int size() { return RT_THREADS; }
+  __device__ static void sync() { __syncthreads(); }
+  __device__ static int any(int v) { return __syncthreads_or(v); }
+  __device__ static float max(float v, float* scratch) {   // v >= 0
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if (threadIdx.x == 0) *scratch = 0.f;
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) atomicMax(reinterpret_cast<int*>(scratch), __float_as_int(v));
+    __syncthreads();
+    const float r = *scratch;
+    __syncthreads();
+    return r;
+  }
+};
+
+// SVD of one block by a team (one warp, or the CTA for large blocks), mixed precision.
+// Bm (m x n column-major, n <= m, scaled to max |entry| = 1) is left untouched;
+// on return W = Bm Q with mutually orthogonal columns (FP64) and Q (n x n)
+// orthogonal to FP64 precision.  Steps: FP32 one-sided Jacobi on a copy of Bm
+// until the columns are orthogonal at FP32 level; Q = Newton-Schulz
+// orthogonalisation of the FP32 rotations in FP64; W = Bm Q in FP64; FP64
+// one-sided Jacobi sweeps from that nearly orthogonal start (rotation angles
+// computed in FP32, cos/sin normalised in FP64 so every rotation is orthogonal
+// in FP64).  Column pairs of a tournament round go to the team's 8-lane groups.
 // Returns 1 if a phase hit the sweep limit.
-__device__ int block_svd_warp(const double* __restrict__ Bm, double* __restrict__ W, double* __restrict__ Q,
-                              float* __restrict__ W32, float* __restrict__ Q32, double* __restrict__ T, int m,
-                              int n, int max_sweeps) {
-  const int lane = threadIdx.x & 31, grp = lane >> 3, gl = lane & 7;
-  const unsigned gmask = 0xffu << (grp * 8);
+template <class Team>
+__device__ int block_svd(const double* __restrict__ Bm, double* __restrict__ W, double* __restrict__ Q,
+                         float* __restrict__ W32, float* __restrict__ Q32, double* __restrict__ T, int m, int n,
+                         int max_sweeps, float* fscratch) {
+  const int tr = Team::rank(), ts = Team::size();
+  const int lane = threadIdx.x & 31, grp = tr >> 3, ngrp = ts >> 3, gl = tr & 7;
+  const unsigned gmask = 0xffu << ((lane >> 3) * 8);
   const int n2 = n + (n & 1);
   int noconv = 0;
   // ---- FP32 phase
-  for (int idx = lane; idx < m * n; idx += 32) W32[idx] = (float)Bm[idx];
-  for (int idx = lane; idx < n * n; idx += 32) Q32[idx] = (idx / n == idx % n) ? 1.f : 0.f;
-  __syncwarp();
+  for (int idx = tr; idx < m * n; idx += ts) W32[idx] = (float)Bm[idx];
+  for (int idx = tr; idx < n * n; idx += ts) Q32[idx] = (idx / n == idx % n) ? 1.f : 0.f;
+  Team::sync();
   if (n >= 2) {
     const float tol32 = 1.2e-7f * (float)m;
     int done = 0;
     for (int sweep = 0; sweep < max_sweeps && !done; ++sweep) {
       int rot = 0;
       for (int r = 0; r < n2 - 1; ++r) {
-        for (int k = grp; k < n2 / 2; k += 4) {
+        for (int k = grp; k < n2 / 2; k += ngrp) {
           int i, j;
           tour_pair(r, k, n2, i, j);
           if (i >= n || j >= n) continue;
@@ -205,17 +238,17 @@ __device__ int block_svd_warp(const double* __restrict__ Bm, double* __restrict_
           }
           rot = 1;
         }
-        __syncwarp();
+        Team::sync();
       }
-      done = !__any_sync(0xffffffffu, rot);
+      done = !Team::any(rot);
     }
   }
   // ---- Q = orthogonalised FP32 rotations: Newton-Schulz Q <- Q (1.5 I - 0.5 Q^T Q) in FP64,
   // twice: the FP32 product is orthogonal to ~1e-6, each step squares the defect
-  for (int idx = lane; idx < n * n; idx += 32) Q[idx] = (double)Q32[idx];
-  __syncwarp();
+  for (int idx = tr; idx < n * n; idx += ts) Q[idx] = (double)Q32[idx];
+  Team::sync();
   for (int it = 0; it < 2; ++it) {
-    for (int idx = lane; idx < n * n; idx += 32) {
+    for (int idx = tr; idx < n * n; idx += ts) {
       const int i = idx % n, j = idx / n;
       const double* qi = Q + (size_t)i * n;
       const double* qj = Q + (size_t)j * n;
@@ -223,35 +256,38 @@ __device__ int block_svd_warp(const double* __restrict__ Bm, double* __restrict_
       for (int k = 0; k < n; ++k) acc = fma(qi[k], qj[k], acc);
       T[idx] = (i == j ? 1.5 : 0.0) - 0.5 * acc;
     }
-    __syncwarp();
-    for (int idx = lane; idx < n * n; idx += 32) {
+    Team::sync();
+    for (int idx = tr; idx < n * n; idx += ts) {
       const int row = idx % n, col = idx / n;
       double acc = 0.0;
       for (int k = 0; k < n; ++k) acc = fma(Q[(size_t)k * n + row], T[(size_t)col * n + k], acc);
       W[idx] = acc;                                // W used as temporary (m*n >= n*n)
     }
-    __syncwarp();
-    for (int idx = lane; idx < n * n; idx += 32) Q[idx] = W[idx];
-    __syncwarp();
+    Team::sync();
+    for (int idx = tr; idx < n * n; idx += ts) Q[idx] = W[idx];
+    Team::sync();
   }
   // ---- W = Bm Q
-  for (int idx = lane; idx < m * n; idx += 32) {
+  for (int idx = tr; idx < m * n; idx += ts) {
     const int row = idx % m, col = idx / m;
     const double* qc = Q + (size_t)col * n;
     double acc = 0.0;
     for (int k = 0; k < n; ++k) acc = fma(Bm[(size_t)k * m + row], qc[k], acc);
     W[idx] = acc;
   }
-  __syncwarp();
+  Team::sync();
   if (n < 2) return noconv;
-  // ---- FP64 phase
+  // ---- FP64 phase.  A sweep that finds no pair above 1e-7 relative leaves
+  // off-diagonals near 1e-14 after its own rotations (quadratic convergence),
+  // so the loop ends after that sweep without a confirming one.
   const double tol64 = 2.220446049250313e-16 * (double)m;
   const float tol64sq = (float)(tol64 * tol64);
   noconv = 1;
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     int rot = 0;
+    float worst = 0.f;                             // largest gamma^2 / (alpha beta) seen this sweep
     for (int r = 0; r < n2 - 1; ++r) {
-      for (int k = grp; k < n2 / 2; k += 4) {
+      for (int k = grp; k < n2 / 2; k += ngrp) {
         int i, j;
         tour_pair(r, k, n2, i, j);
         if (i >= n || j >= n) continue;
@@ -272,6 +308,7 @@ __device__ int block_svd_warp(const double* __restrict__ Bm, double* __restrict_
         const double sc = exp2_neg_exponent(fmax(al, be));
         const float af = (float)(al * sc), bf = (float)(be * sc), gf = (float)(ga * sc);
         if (!(gf * gf > tol64sq * af * bf)) continue;
+        worst = fmaxf(worst, (gf * gf) / (af * bf));
         const float zeta = (bf - af) / (2.f * gf);
         const float t32 = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + hypotf(1.f, zeta));
         const double t = (double)t32, w = fma(t, t, 1.0);
@@ -294,9 +331,10 @@ __device__ int block_svd_warp(const double* __restrict__ Bm, double* __restrict_
         }
         rot = 1;
       }
-      __syncwarp();
+      Team::sync();
     }
-    if (!__any_sync(0xffffffffu, rot)) {
+    worst = Team::max(worst, fscratch);
+    if (!Team::any(rot) || worst <= 1e-14f) {
       noconv = 0;
       break;
     }
@@ -317,7 +355,8 @@ __global__ void __launch_bounds__(RT_THREADS) rotate_pairs_kernel(const RotDesc*
   __shared__ double sig[MAXSIG];
   __shared__ unsigned char sig_keep[MAXSIG];
   __shared__ short s_ord[MAXBLK];
-  __shared__ int s_nblk, s_nnew, s_total, s_nsig, s_keep, s_status;
+  __shared__ int s_nblk, s_nnew, s_total, s_nsig, s_keep, s_status, s_nbig;
+  __shared__ float s_fmax;
   __shared__ double s_disc, s_red[RT_WARPS], s_flops;
 
   ThetaBlk* tb = reinterpret_cast<ThetaBlk*>(D.meta);
@@ -491,8 +530,77 @@ __global__ void __launch_bounds__(RT_THREADS) rotate_pairs_kernel(const RotDesc*
       s_ord[rank] = (short)b;
     }
     __syncthreads();
-    // ---- SVD of every block, one warp per block
-    for (int bi = warp; bi < nnew; bi += RT_WARPS) {
+    // ---- SVD of every block: large blocks by the whole CTA one after another,
+    // the rest one warp per block
+    if (tid == 0) {
+      int nb_big = 0;
+      while (nb_big < nnew) {
+        const NewBlk& B = nb[s_ord[nb_big]];
+        if ((B.nr < B.nc ? B.nr : B.nc) < BIG_BLOCK_N) break;
+        ++nb_big;
+      }
+      s_nbig = nb_big;
+    }
+    __syncthreads();
+    const int nbig = s_nbig;
+    for (int bi = 0; bi < nbig; ++bi) {
+      const int b = s_ord[bi];
+      const NewBlk B = nb[b];
+      const bool trans = B.nc > B.nr;
+      const int m = trans ? B.nc : B.nr, n = trans ? B.nr : B.nc;
+      double* Bm = D.bbuf + B.wofs;
+      double* W = D.wbuf + B.wofs;
+      float* W32 = D.w32 + B.wofs;
+      double* Q = D.qbuf + B.qofs;
+      double* T = D.tbuf + B.qofs;
+      float* Q32 = D.q32 + B.qofs;
+      double mx = 0.0;
+      for (int idx = tid; idx < m * n; idx += RT_THREADS) {
+        const int wi = idx % m, wj = idx / m;
+        const int br = trans ? wj : wi, bc = trans ? wi : wj;
+        int k1p = 3, k2p = 3;
+        while (k1p > 0 && (B.rowsec[k1p] < 0 || B.rowoff[k1p] > br)) --k1p;
+        while (k2p > 0 && (B.colsec[k2p] < 0 || B.coloff[k2p] > bc)) --k2p;
+        const int sL = B.rowsec[k1p], sR = B.colsec[k2p];
+        const int l = secL.off[sL] + (br - B.rowoff[k1p]);
+        const int r = secR.off[sR] + (bc - B.coloff[k2p]);
+        const int Kp = k1p * 4 + k2p;
+        double acc = 0.0;
+        for (int e = 0; e < gnz_n[Kp]; ++e) {
+          const int K = gnz_k[Kp][e];
+          const int k1 = K >> 2, k2 = K & 3;
+          const int qM = qadd(secL.q[sL], local_charge(k1));
+          if (qM < 0 || lutM[qM] < 0) continue;
+          acc = fma(gnz_v[Kp][e], D.theta[(((size_t)l * 4 + k1) * 4 + k2) * chr + r], acc);
+        }
+        Bm[idx] = acc;
+        mx = fmax(mx, fabs(acc));
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      if (lane == 0) s_red[warp] = mx;
+      __syncthreads();
+      double bmax = 0.0;
+      for (int w2 = 0; w2 < RT_WARPS; ++w2) bmax = fmax(bmax, s_red[w2]);
+      const double scale = bmax > 0.0 ? bmax : 1.0;
+      const double inv = 1.0 / scale;
+      for (int idx = tid; idx < m * n; idx += RT_THREADS) Bm[idx] *= inv;
+      if (tid == 0) nb[b].scale = scale;
+      __syncthreads();
+      const int ncv = block_svd<CtaTeam>(Bm, W, Q, W32, Q32, T, m, n, D.max_sweeps, &s_fmax);
+      if (ncv && tid == 0) atomicOr(&s_status, STATUS_NOCONV | (min(m, 4095) << 8) | (min(n, 4095) << 20));
+      for (int j = warp; j < n; j += RT_WARPS) {
+        double acc = 0.0;
+        for (int u = lane; u < m; u += 32) {
+          const double v = W[(size_t)j * m + u];
+          acc = fma(v, v, acc);
+        }
+        acc = warp_sum(acc);
+        if (lane == 0) sig[B.sofs + j] = sqrt(acc) * scale;
+      }
+      __syncthreads();
+    }
+    for (int bi = nbig + warp; bi < nnew; bi += RT_WARPS) {
       const int b = s_ord[bi];
       const NewBlk B = nb[b];
       const bool trans = B.nc > B.nr;                // work on B^T so that n <= m
@@ -533,7 +641,7 @@ __global__ void __launch_bounds__(RT_THREADS) rotate_pairs_kernel(const RotDesc*
       for (int idx = lane; idx < m * n; idx += 32) Bm[idx] *= inv;
       if (lane == 0) nb[b].scale = scale;
       __syncwarp();
-      const int ncv = block_svd_warp(Bm, W, Q, W32, Q32, T, m, n, D.max_sweeps);
+      const int ncv = block_svd<WarpTeam>(Bm, W, Q, W32, Q32, T, m, n, D.max_sweeps, nullptr);
       if (ncv && lane == 0) atomicOr(&s_status, STATUS_NOCONV | (min(m, 4095) << 8) | (min(n, 4095) << 20));
       for (int j = 0; j < n; ++j) {
         double acc = 0.0;
