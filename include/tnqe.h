@@ -46,10 +46,26 @@ typedef enum {
   TNQE_ERR_NUMERIC = 7   /* NaN/Inf in an output */
 } tnqe_status;
 
+/* Contraction precision.  The rotation SVDs and the solve are FP64 always.
+ * TF32X3: FP32 environments; GEMM operands split into TF32 high and low parts,
+ *   three products (hi.hi + hi.lo + lo.hi) accumulated in FP32 on the tensor cores;
+ *   stage 2 in FP32.  About 21 bits per operand, FP32 rounding in every sum.
+ * BF16X3 / BF16X6 / BF16X10 / BF16X15: double-float environments (two FP32
+ *   values, about 48 bits); every GEMM operand row is scaled by a power of two
+ *   and split into S = 2 / 3 / 4 / 5 fixed-point BF16 slices of 8 bits each; the
+ *   3 / 6 / 10 / 15 slice products of order <= S + 1 run on the tensor cores with
+ *   FP32 accumulation that is exact for the three leading products (integer
+ *   multiples of a power of two, bounded by 2^24 for K <= 1024); stage 2 in
+ *   double-float arithmetic.  The error is the slicing truncation alone:
+ *   about 2^-16, 2^-24, 2^-32, 2^-40 of the row maxima.  Bond dimensions above 256
+ *   return TNQE_ERR_ARG in these modes. */
 typedef enum {
-  TNQE_PREC_FP64 = 0,    /* every step in FP64 */
-  TNQE_PREC_TF32X3 = 1,  /* transfer contractions as 3-term split TF32 products, FP32 accumulation */
-  TNQE_PREC_BF16X3 = 2   /* transfer contractions as 3-term split BF16 products, FP32 accumulation */
+  TNQE_PREC_FP64 = 0,
+  TNQE_PREC_TF32X3 = 1,
+  TNQE_PREC_BF16X3 = 2,
+  TNQE_PREC_BF16X6 = 3,
+  TNQE_PREC_BF16X10 = 4,
+  TNQE_PREC_BF16X15 = 5
 } tnqe_precision;
 
 typedef struct {
@@ -125,13 +141,17 @@ tnqe_status tnqe_set_precision(tnqe_ctx* ctx, int precision);
  * launches: number of kernels that call launched. */
 tnqe_status tnqe_last_timing(const tnqe_ctx* ctx, double* times, int* launches);
 
-/* Per-kernel profile of the last tnqe_matrix_elements call (n values written, n <= 10):
+/* Per-kernel profile of the last tnqe_matrix_elements call (n values written,
+ * n <= TNQE_PROFILE_LEN):
  * [0] rotation kernel ms, [1] stage-1 GEMM ms (X = L B), [2] stage-2 MPO ms,
  * [3] stage-3 GEMM ms (L' = A^T Y), [4] rotation algorithmic FLOPs
  * (two-site contraction + gate + 4mn^2 + 8n^3 per SVD block), [5] stage-1 FLOPs,
  * [6] stage-2 algorithmic bytes (X read once, Y written once), [7] stage-3 FLOPs,
- * [8] stage-2 FLOPs, [9] kernels launched.  Times come from CUDA events on the
- * context stream around each launch and are summed over sites. */
+ * [8] stage-2 FLOPs, [9] kernels launched, [10] slicing kernels ms and
+ * [11] slicing algorithmic bytes (BF16X* modes: source read once, slices
+ * written once).  Times come from CUDA events on the context stream around
+ * each launch and are summed over sites. */
+#define TNQE_PROFILE_LEN 12
 tnqe_status tnqe_last_profile(const tnqe_ctx* ctx, double* prof, int n);
 
 /* ---------------------------------------------------------------------------

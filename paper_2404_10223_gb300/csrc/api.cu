@@ -16,6 +16,7 @@
 
 #include "../../include/tnqe.h"
 #include "internal.h"
+#include "oz_gemm.cuh"
 #include "tc_gemm.cuh"
 
 using namespace tnqe;
@@ -90,6 +91,7 @@ struct DevMps {
   std::vector<int*> d_rowptr, d_col;
   std::vector<double*> d_val;
   std::vector<float*> d_val32;
+  std::vector<float2*> d_valdf;          // (hi, lo) FP32 pairs of the MPO values
   std::vector<void*> owned;
   void free_all() {
     for (void* p : owned) cudaFree(p);
@@ -122,6 +124,7 @@ struct tnqe_ctx {
   // contraction workspace
   DBuf con_ws, con_desc, con_out;
   DBuf tc_ws, tc_desc, tc_err;
+  DBuf oz_ws, oz_desc;
   // last tnqe_rotate result
   int kept_pair_valid = 0;
   std::vector<int> kept_dims;
@@ -131,7 +134,7 @@ struct tnqe_ctx {
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
   // per-kernel profile of the last matrix-element call (see tnqe_last_profile)
   std::vector<cudaEvent_t> pev;
-  double prof[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  double prof[TNQE_PROFILE_LEN] = {};
 };
 
 namespace {
@@ -518,7 +521,7 @@ void run_contractions(tnqe_ctx* c, const std::vector<std::pair<int, int>>& pairs
     size_t i1 = 0, i3 = 0, is = 0, ip1 = 0, ip3 = 0, ips = 0;
     for (int t = 0; t < N; ++t) {
       const int n1 = g1n[t], n3 = g3n[t], ns = spn[t];
-      cudaEvent_t* E = &c->pev[2 + 4 * t];
+      cudaEvent_t* E = &c->pev[2 + 6 * t];
       CK(cudaEventRecord(E[0], c->stream));
       CKL(launch_gemm_f64(reinterpret_cast<GemmDesc*>(dd + o1) + i1, reinterpret_cast<long long*>(dd + op1) + ip1,
                           n1, g1pre[ip1 + n1], c->stream));
@@ -541,7 +544,7 @@ void run_contractions(tnqe_ctx* c, const std::vector<std::pair<int, int>>& pairs
     c->launches += 1;
     CK(cudaStreamSynchronize(c->stream));   // the next wave reuses the workspace and the events
     for (int t = 0; t < N; ++t) {
-      cudaEvent_t* E = &c->pev[2 + 4 * t];
+      cudaEvent_t* E = &c->pev[2 + 6 * t];
       float a = 0.f, b = 0.f, d = 0.f;
       CK(cudaEventElapsedTime(&a, E[0], E[1]));
       CK(cudaEventElapsedTime(&b, E[1], E[2]));
@@ -768,7 +771,7 @@ void run_contractions_tc(tnqe_ctx* c, const std::vector<std::pair<int, int>>& pa
     size_t i1 = 0, i3 = 0, is = 0, ip1 = 0, ip3 = 0, ips = 0;
     for (int t = 0; t < N; ++t) {
       const int n1 = g1n[t], n3 = g3n[t], ns = spn[t];
-      cudaEvent_t* E = &c->pev[2 + 4 * t];
+      cudaEvent_t* E = &c->pev[2 + 6 * t];
       CK(cudaEventRecord(E[0], c->stream));
       CKL(launch_gemm_tf32x3(reinterpret_cast<TcGemmDesc*>(dd + o1) + i1, reinterpret_cast<long long*>(dd + op1) + ip1,
                              n1, g1pre[ip1 + n1], c->opt.max_spin, derr, c->stream));
@@ -791,7 +794,7 @@ void run_contractions_tc(tnqe_ctx* c, const std::vector<std::pair<int, int>>& pa
     c->launches += 1;
     CK(cudaStreamSynchronize(c->stream));
     for (int t = 0; t < N; ++t) {
-      cudaEvent_t* E = &c->pev[2 + 4 * t];
+      cudaEvent_t* E = &c->pev[2 + 6 * t];
       float a = 0.f, b = 0.f, d = 0.f;
       CK(cudaEventElapsedTime(&a, E[0], E[1]));
       CK(cudaEventElapsedTime(&b, E[1], E[2]));
@@ -799,6 +802,288 @@ void run_contractions_tc(tnqe_ctx* c, const std::vector<std::pair<int, int>>& pa
       c->prof[1] += a;
       c->prof[2] += b;
       c->prof[3] += d;
+    }
+    p0 = p1;
+  }
+  int herr = 0;
+  CK(cudaMemcpy(&herr, c->tc_err.p, sizeof(int), cudaMemcpyDeviceToHost));
+  if (herr) throw Error(TNQE_ERR_TIMEOUT, "a tensor-core pipeline wait ran out of iterations");
+}
+
+
+// ----------------------------------------------------------------------------- sliced-BF16 contraction
+inline long long ld8(long long x) { return (x + 7) & ~7LL; }
+inline size_t lz8(size_t x) { return (x + 7) & ~(size_t)7; }
+inline size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// 3-D BF16 tensor map over slices [ns][rows][ldK] (K contiguous), box {32, 128, ns}, 64-byte swizzle
+void encode_slices(CUtensorMap* map, const __nv_bfloat16* base, long long rows, long long K, long long ldK, int ns) {
+  cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)rows, (cuuint64_t)ns};
+  cuuint64_t strides[2] = {(cuuint64_t)ldK * 2, (cuuint64_t)rows * ldK * 2};
+  cuuint32_t box[3] = {(cuuint32_t)OZ_BK, (cuuint32_t)OZ_BM, (cuuint32_t)ns};
+  cuuint32_t es[3] = {1, 1, 1};
+  const CUresult r = tensor_map_encoder()(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3,
+                                          const_cast<__nv_bfloat16*>(base), dims, strides, box, es,
+                                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                                          CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) throw Error(TNQE_ERR_CUDA, "cuTensorMapEncodeTiled (slices) failed: " + std::to_string((int)r));
+}
+
+int slices_of(int precision) {
+  return precision == TNQE_PREC_BF16X3 ? 2 : precision == TNQE_PREC_BF16X6 ? 3 : precision == TNQE_PREC_BF16X10 ? 4 : 5;
+}
+
+void run_contractions_oz(tnqe_ctx* c, const std::vector<std::pair<int, int>>& pairs, const std::vector<KetView>& kets,
+                         double* d_H, double* d_S) {
+  const int N = c->N;
+  const int np = (int)pairs.size();
+  const int ns = slices_of(c->opt.precision);
+  // per-pair workspace (bytes): environment, X / B-slices, Y / A-slices, exponents, site slices
+  std::vector<size_t> envb(np), xbb(np), yab(np), expb(np), siteb(np);
+  for (int p = 0; p < np; ++p) {
+    const DevMps& bi = *c->mps[pairs[p].first];
+    const KetView& kv = kets[p];
+    size_t e = 8, xb = 8, ya = 8, ex = 4, st = 0;
+    for (int t = 0; t <= N; ++t) e = std::max(e, (size_t)bi.dims[t] * bi.mpo.dims[t] * kv.dims[t] * 8);
+    for (int t = 0; t < N; ++t) {
+      const size_t ca = bi.dims[t], ca2 = bi.dims[t + 1], cb = kv.dims[t], cb2 = kv.dims[t + 1];
+      const size_t Din = bi.mpo.dims[t], Dout = bi.mpo.dims[t + 1];
+      if (4 * ca > (size_t)OZ_MAXK || cb > (size_t)OZ_MAXK)
+        throw Error(TNQE_ERR_ARG, "sliced BF16 contraction needs bond dimensions <= 256");
+      xb = std::max(xb, std::max(ca * Din * 4 * cb2 * 8, (size_t)ns * Dout * cb2 * lz8(4 * ca) * 2));
+      ya = std::max(ya, std::max(ca * 4 * Dout * cb2 * 8, (size_t)ns * ca * Din * lz8(cb) * 2));
+      ex = std::max(ex, std::max(ca * Din, Dout * cb2) * 4);
+      st += al256((size_t)ns * 4 * cb2 * lz8(cb) * 2) + al256(4 * cb2 * 4) + al256((size_t)ns * ca2 * lz8(4 * ca) * 2) +
+            al256(ca2 * 4);
+    }
+    envb[p] = al256(e);
+    xbb[p] = al256(xb);
+    yab[p] = al256(ya);
+    expb[p] = 2 * al256(ex);
+    siteb[p] = st;
+  }
+  size_t freeb = 0, totalb = 0;
+  CK(cudaMemGetInfo(&freeb, &totalb));
+  const double budget = 0.6 * (double)(freeb + c->oz_ws.cap);
+  c->tc_err.ensure(256);
+  CK(cudaMemsetAsync(c->tc_err.p, 0, sizeof(int), c->stream));
+  int* derr = c->tc_err.as<int>();
+  size_t p0 = 0;
+  while (p0 < (size_t)np) {
+    size_t p1 = p0;
+    double need = 0.0;
+    while (p1 < (size_t)np) {
+      const double add = (double)(envb[p1] + xbb[p1] + yab[p1] + expb[p1] + siteb[p1]);
+      if (p1 > p0 && need + add > budget) break;
+      need += add;
+      ++p1;
+    }
+    const int nw = (int)(p1 - p0);
+    c->oz_ws.ensure((size_t)need + 1024);
+    unsigned char* base =
+        reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(c->oz_ws.p) + 255) & ~(uintptr_t)255);
+    std::vector<float2*> env(nw), X(nw), Y(nw);
+    std::vector<__nv_bfloat16*> Bsl(nw), Asl(nw);
+    std::vector<int*> expA(nw), expB(nw);
+    std::vector<std::vector<__nv_bfloat16*>> ketS(nw, std::vector<__nv_bfloat16*>(N)), braS(nw, std::vector<__nv_bfloat16*>(N));
+    std::vector<std::vector<int*>> ketE(nw, std::vector<int*>(N)), braE(nw, std::vector<int*>(N));
+    std::vector<SliceSiteDesc> sites;
+    std::vector<long long> sitepre;
+    long long siterows = 0;
+    {
+      size_t o = 0;
+      for (int w = 0; w < nw; ++w) {
+        const int p = (int)p0 + w;
+        const DevMps& bi = *c->mps[pairs[p].first];
+        const KetView& kv = kets[p];
+        env[w] = reinterpret_cast<float2*>(base + o); o += envb[p];
+        X[w] = reinterpret_cast<float2*>(base + o);
+        Bsl[w] = reinterpret_cast<__nv_bfloat16*>(base + o); o += xbb[p];
+        Y[w] = reinterpret_cast<float2*>(base + o);
+        Asl[w] = reinterpret_cast<__nv_bfloat16*>(base + o); o += yab[p];
+        expA[w] = reinterpret_cast<int*>(base + o); o += expb[p] / 2;
+        expB[w] = reinterpret_cast<int*>(base + o); o += expb[p] / 2;
+        for (int t = 0; t < N; ++t) {
+          const int ca = bi.dims[t], ca2 = bi.dims[t + 1], cb = kv.dims[t], cb2 = kv.dims[t + 1];
+          ketS[w][t] = reinterpret_cast<__nv_bfloat16*>(base + o); o += al256((size_t)ns * 4 * cb2 * lz8(cb) * 2);
+          ketE[w][t] = reinterpret_cast<int*>(base + o); o += al256((size_t)4 * cb2 * 4);
+          braS[w][t] = reinterpret_cast<__nv_bfloat16*>(base + o); o += al256((size_t)ns * ca2 * lz8(4 * ca) * 2);
+          braE[w][t] = reinterpret_cast<int*>(base + o); o += al256((size_t)ca2 * 4);
+          SliceSiteDesc k{kv.base + kv.off[t], ketS[w][t], ketE[w][t], ld8(cb), (long long)4 * cb2 * ld8(cb), cb, cb2, 0, ns};
+          sitepre.push_back(siterows);
+          siterows += 4LL * cb2;
+          sites.push_back(k);
+          SliceSiteDesc b{bi.d_t + bi.off[t], braS[w][t], braE[w][t], ld8(4 * ca), (long long)ca2 * ld8(4 * ca), ca, ca2,
+                          1, ns};
+          sitepre.push_back(siterows);
+          siterows += ca2;
+          sites.push_back(b);
+        }
+      }
+    }
+    std::vector<SliceRowsDesc> sa;
+    std::vector<SliceColsDesc> sb;
+    std::vector<OzGemmDesc> g1, g3;
+    std::vector<SpmmDfDesc> sp;
+    std::vector<long long> sapre, sbpre, g1pre, g3pre, sppre;
+    double slice_bytes = 0.0;
+    for (int t = 0; t < N; ++t) {
+      long long rowsA = 0, blocksB = 0, tiles1 = 0, tiles3 = 0, tasks = 0;
+      for (int w = 0; w < nw; ++w) {
+        const int p = (int)p0 + w;
+        const DevMps& bi = *c->mps[pairs[p].first];
+        const KetView& kv = kets[p];
+        const int ca = bi.dims[t], ca2 = bi.dims[t + 1], cb = kv.dims[t], cb2 = kv.dims[t + 1];
+        const int Din = bi.mpo.dims[t], Dout = bi.mpo.dims[t + 1];
+        const long long MA = (long long)ca * Din;
+        // A slices: environment rows (a, w) over b
+        SliceRowsDesc a{env[w], Asl[w], expA[w], cb, ld8(cb), MA * ld8(cb), cb, ns};
+        sapre.push_back(rowsA);
+        rowsA += MA;
+        sa.push_back(a);
+        slice_bytes += (double)MA * cb * (8.0 + 2.0 * ns);
+        OzGemmDesc d1;
+        std::memset(&d1, 0, sizeof(d1));
+        d1.M = (int)MA;
+        d1.N = 4 * cb2;
+        d1.K = cb;
+        encode_slices(&d1.mapA, Asl[w], MA, cb, ld8(cb), ns);
+        encode_slices(&d1.mapB, ketS[w][t], 4LL * cb2, cb, ld8(cb), ns);
+        d1.ea = expA[w];
+        d1.eb = ketE[w][t];
+        d1.C = X[w];
+        d1.ldc = d1.N;
+        d1.cg = d1.N;
+        d1.cld = 0;
+        d1.tiles_n = (d1.N + OZ_BN - 1) / OZ_BN;
+        d1.nslices = ns;
+        g1pre.push_back(tiles1);
+        tiles1 += (long long)((d1.M + OZ_BM - 1) / OZ_BM) * d1.tiles_n;
+        g1.push_back(d1);
+        SpmmDfDesc s{};
+        s.chi_a = ca;
+        s.nrows = 4 * Dout;
+        s.ncols_x = 4 * Din;
+        s.width = cb2;
+        s.rowptr = bi.d_rowptr[t];
+        s.col = bi.d_col[t];
+        s.val = bi.d_valdf[t];
+        s.X = X[w];
+        s.Y = Y[w];
+        sppre.push_back(tasks);
+        tasks += (long long)ca * 4 * Dout;
+        sp.push_back(s);
+        // B slices: Y columns (w', b') over (a, k), K-major
+        const long long NB = (long long)Dout * cb2;
+        SliceColsDesc b{Y[w], Bsl[w], expB[w], NB, ld8(4 * ca), NB * ld8(4 * ca), 4 * ca, (int)NB, ns, 0};
+        sbpre.push_back(blocksB);
+        blocksB += (NB + 15) / 16;
+        sb.push_back(b);
+        slice_bytes += (double)NB * 4 * ca * (8.0 + 2.0 * ns);
+        OzGemmDesc d3;
+        std::memset(&d3, 0, sizeof(d3));
+        d3.M = ca2;
+        d3.N = (int)NB;
+        d3.K = 4 * ca;
+        encode_slices(&d3.mapA, braS[w][t], ca2, 4LL * ca, ld8(4 * ca), ns);
+        encode_slices(&d3.mapB, Bsl[w], NB, 4LL * ca, ld8(4 * ca), ns);
+        d3.ea = braE[w][t];
+        d3.eb = expB[w];
+        d3.C = env[w];
+        d3.ldc = NB;
+        d3.cg = d3.N;
+        d3.cld = 0;
+        d3.tiles_n = (d3.N + OZ_BN - 1) / OZ_BN;
+        d3.nslices = ns;
+        g3pre.push_back(tiles3);
+        tiles3 += (long long)((d3.M + OZ_BM - 1) / OZ_BM) * d3.tiles_n;
+        g3.push_back(d3);
+      }
+      sapre.push_back(rowsA);
+      sbpre.push_back(blocksB);
+      g1pre.push_back(tiles1);
+      g3pre.push_back(tiles3);
+      sppre.push_back(tasks);
+    }
+    for (const OzGemmDesc& d : g1) c->prof[5] += 2.0 * d.M * d.N * d.K;
+    for (const OzGemmDesc& d : g3) c->prof[7] += 2.0 * d.M * d.N * d.K;
+    c->prof[11] += slice_bytes;
+    for (int w = 0; w < nw; ++w) {
+      const int p = (int)p0 + w;
+      const DevMps& bi = *c->mps[pairs[p].first];
+      const KetView& kv = kets[p];
+      for (int t = 0; t < N; ++t) {
+        const double ca = bi.dims[t], cb2 = kv.dims[t + 1];
+        c->prof[6] += 8.0 * ca * cb2 * 4.0 * (bi.mpo.dims[t] + bi.mpo.dims[t + 1]);
+        c->prof[8] += 2.0 * (double)bi.mpo.sites[t].val.size() * ca * cb2;
+      }
+    }
+    // one upload: descriptors, prefixes, environment pointers
+    sitepre.push_back(siterows);
+    struct Blob {
+      std::vector<unsigned char> h;
+      size_t put(const void* src, size_t n) {
+        const size_t o = al256(h.size());
+        h.resize(o + al256(n), 0);
+        if (n) std::memcpy(h.data() + o, src, n);
+        return o;
+      }
+    } blob;
+    const size_t o_g1 = blob.put(g1.data(), g1.size() * sizeof(OzGemmDesc));
+    const size_t o_g3 = blob.put(g3.data(), g3.size() * sizeof(OzGemmDesc));
+    const size_t o_sa = blob.put(sa.data(), sa.size() * sizeof(SliceRowsDesc));
+    const size_t o_sb = blob.put(sb.data(), sb.size() * sizeof(SliceColsDesc));
+    const size_t o_sp = blob.put(sp.data(), sp.size() * sizeof(SpmmDfDesc));
+    const size_t o_st = blob.put(sites.data(), sites.size() * sizeof(SliceSiteDesc));
+    const size_t o_g1p = blob.put(g1pre.data(), g1pre.size() * 8);
+    const size_t o_g3p = blob.put(g3pre.data(), g3pre.size() * 8);
+    const size_t o_sap = blob.put(sapre.data(), sapre.size() * 8);
+    const size_t o_sbp = blob.put(sbpre.data(), sbpre.size() * 8);
+    const size_t o_spp = blob.put(sppre.data(), sppre.size() * 8);
+    const size_t o_stp = blob.put(sitepre.data(), sitepre.size() * 8);
+    const size_t o_env = blob.put(env.data(), env.size() * sizeof(float2*));
+    c->oz_desc.ensure(blob.h.size());
+    unsigned char* dd = c->oz_desc.as<unsigned char>();
+    CK(cudaMemcpyAsync(dd, blob.h.data(), blob.h.size(), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaEventRecord(c->pev[2 + 6 * N], c->stream));
+    CKL(launch_unit_env(reinterpret_cast<float2* const*>(dd + o_env), nw, c->stream));
+    CKL(launch_slice_sites(reinterpret_cast<SliceSiteDesc*>(dd + o_st), reinterpret_cast<long long*>(dd + o_stp),
+                           (int)sites.size(), siterows, c->stream));
+    CK(cudaEventRecord(c->pev[3 + 6 * N], c->stream));
+    c->launches += 2;
+    size_t i = 0, ip = 0;
+    for (int t = 0; t < N; ++t, i += nw, ip += nw + 1) {
+      cudaEvent_t* E = &c->pev[2 + 6 * t];
+      auto pre = [&](size_t off) { return reinterpret_cast<long long*>(dd + off) + ip; };
+      CK(cudaEventRecord(E[0], c->stream));
+      CKL(launch_slice_rows(reinterpret_cast<SliceRowsDesc*>(dd + o_sa) + i, pre(o_sap), nw, sapre[ip + nw], c->stream));
+      CK(cudaEventRecord(E[1], c->stream));
+      CKL(launch_gemm_bf16s(reinterpret_cast<OzGemmDesc*>(dd + o_g1) + i, pre(o_g1p), nw, g1pre[ip + nw],
+                            c->opt.max_spin, derr, c->stream));
+      CK(cudaEventRecord(E[2], c->stream));
+      CKL(launch_spmm_df(reinterpret_cast<SpmmDfDesc*>(dd + o_sp) + i, pre(o_spp), nw, sppre[ip + nw], c->stream));
+      CK(cudaEventRecord(E[3], c->stream));
+      CKL(launch_slice_cols(reinterpret_cast<SliceColsDesc*>(dd + o_sb) + i, pre(o_sbp), nw, sbpre[ip + nw], c->stream));
+      CK(cudaEventRecord(E[4], c->stream));
+      CKL(launch_gemm_bf16s(reinterpret_cast<OzGemmDesc*>(dd + o_g3) + i, pre(o_g3p), nw, g3pre[ip + nw],
+                            c->opt.max_spin, derr, c->stream));
+      CK(cudaEventRecord(E[5], c->stream));
+      c->launches += 5;
+    }
+    CKL(launch_extract_df(reinterpret_cast<const float2* const*>(dd + o_env), nw, d_H + p0, d_S + p0, c->stream));
+    c->launches += 1;
+    CK(cudaStreamSynchronize(c->stream));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, c->pev[2 + 6 * N], c->pev[3 + 6 * N]));
+    c->prof[10] += ms;
+    for (int t = 0; t < N; ++t) {
+      cudaEvent_t* E = &c->pev[2 + 6 * t];
+      float x[5];
+      for (int k = 0; k < 5; ++k) CK(cudaEventElapsedTime(&x[k], E[k], E[k + 1]));
+      c->prof[10] += x[0] + x[3];
+      c->prof[1] += x[1];
+      c->prof[2] += x[2];
+      c->prof[3] += x[4];
     }
     p0 = p1;
   }
@@ -926,6 +1211,13 @@ void prepare_mps(tnqe_ctx* c, const double* const* tensors, const int* bond_dims
     m.d_val.push_back(dalloc_copy(m.mpo.sites[t].val, m.owned));
     std::vector<float> v32(m.mpo.sites[t].val.begin(), m.mpo.sites[t].val.end());
     m.d_val32.push_back(dalloc_copy(v32, m.owned));
+    std::vector<float2> vdf(v32.size());
+    for (size_t e = 0; e < v32.size(); ++e) {
+      const double v = m.mpo.sites[t].val[e];
+      vdf[e].x = (float)v;
+      vdf[e].y = (float)(v - (double)vdf[e].x);
+    }
+    m.d_valdf.push_back(dalloc_copy(vdf, m.owned));
   }
 }
 
@@ -959,7 +1251,7 @@ tnqe_status tnqe_create(const double* h1, const double* eri, int N, int n_alpha,
       throw Error(TNQE_ERR_ARG, "electron counts must be in [0, min(N, 14)]");
     c = new tnqe_ctx();
     if (opt) c->opt = *opt; else tnqe_default_options(&c->opt);
-    if (c->opt.precision < 0 || c->opt.precision > 2) throw Error(TNQE_ERR_ARG, "unknown precision");
+    if (c->opt.precision < 0 || c->opt.precision > TNQE_PREC_BF16X15) throw Error(TNQE_ERR_ARG, "unknown precision");
     c->N = N;
     c->na = n_alpha;
     c->nb = n_beta;
@@ -983,7 +1275,7 @@ tnqe_status tnqe_create(const double* h1, const double* eri, int N, int n_alpha,
       c->own_stream = true;
     }
     for (auto& e : c->ev) CK(cudaEventCreate(&e));
-    c->pev.assign(2 + 4 * N, nullptr);
+    c->pev.assign(4 + 6 * N, nullptr);
     for (auto& e : c->pev) CK(cudaEventCreate(&e));
     *out = c;
     return TNQE_OK;
@@ -1103,8 +1395,6 @@ tnqe_status tnqe_matrix_elements(tnqe_ctx* c, const int* pairs, int npairs, doub
       if (i > j) throw Error(TNQE_ERR_ARG, "pairs must have i <= j");
       pl[p] = {i, j};
     }
-    if (c->opt.precision == TNQE_PREC_BF16X3)
-      throw Error(TNQE_ERR_ARG, "the BF16x3 contraction is not built; use TNQE_PREC_FP64 or TNQE_PREC_TF32X3");
     c->launches = 0;
     c->kept_pair_valid = 0;
     for (double& x : c->prof) x = 0.0;
@@ -1136,6 +1426,7 @@ tnqe_status tnqe_matrix_elements(tnqe_ctx* c, const int* pairs, int npairs, doub
     double* dH = c->con_out.as<double>();
     double* dS = dH + npairs;
     if (c->opt.precision == TNQE_PREC_TF32X3) run_contractions_tc(c, pl, kets, dH, dS);
+    else if (c->opt.precision >= TNQE_PREC_BF16X3) run_contractions_oz(c, pl, kets, dH, dS);
     else run_contractions(c, pl, kets, dH, dS);
     CK(cudaEventRecord(c->ev[3], c->stream));
     const bool hdev = is_device_ptr(H_out), sdev = is_device_ptr(S_out);
@@ -1198,7 +1489,7 @@ tnqe_status tnqe_solve(tnqe_ctx* c, const double* H, const double* S, int M, dou
 
 tnqe_status tnqe_set_precision(tnqe_ctx* c, int precision) {
   if (!c) return TNQE_ERR_ARG;
-  if (precision < 0 || precision > 2) {
+  if (precision < 0 || precision > TNQE_PREC_BF16X15) {
     c->err = "unknown precision";
     return TNQE_ERR_ARG;
   }
@@ -1216,7 +1507,7 @@ tnqe_status tnqe_last_timing(const tnqe_ctx* c, double* times, int* launches) {
 
 tnqe_status tnqe_last_profile(const tnqe_ctx* c, double* prof, int n) {
   if (!c || !prof || n < 0) return TNQE_ERR_ARG;
-  for (int k = 0; k < n && k < 10; ++k) prof[k] = c->prof[k];
+  for (int k = 0; k < n && k < TNQE_PROFILE_LEN; ++k) prof[k] = c->prof[k];
   if (n > 9) prof[9] = c->launches;
   return TNQE_OK;
 }

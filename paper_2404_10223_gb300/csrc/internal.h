@@ -1,5 +1,8 @@
 // Internal declarations shared by the host planner, the kernels and the ABI layer.
 #pragma once
+#include <cuda_bf16.h>
+#include <vector_types.h>
+
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -117,6 +120,38 @@ struct SpmmTDesc {                // Yt[(w',b')][(a,k)] = sum W[(w',k),(w,k')] X
 };
 struct TcGemmDesc;
 
+// sliced-BF16 contraction (kernels_oz.cu); double-floats are float2 (hi, lo)
+struct SliceRowsDesc {            // rows of src (K values, stride ld) -> dst[s * slice_stride + r * ldK + k]
+  const float2* src;
+  __nv_bfloat16* dst;
+  int* exps;
+  long long ld, ldK, slice_stride;
+  int K, ns;
+};
+struct SliceColsDesc {            // columns of src[K][ncols] (row stride ld) -> K-major slices per column
+  const float2* src;
+  __nv_bfloat16* dst;
+  int* exps;
+  long long ld, ldK, slice_stride;
+  int K, ncols, ns, pad;
+};
+struct SliceSiteDesc {            // FP64 site tensor [cl][4][cr] -> K-major slices (mode 0 ket, 1 bra)
+  const double* src;
+  __nv_bfloat16* dst;
+  int* exps;
+  long long ldK, slice_stride;
+  int cl, cr, mode, ns;
+};
+struct SpmmDfDesc {               // Y[a][row][:] = sum val * X[a][col][:] in double-float
+  int chi_a, nrows, ncols_x, width;
+  const int* rowptr;
+  const int* col;
+  const float2* val;
+  const float2* X;
+  float2* Y;
+};
+struct OzGemmDesc;
+
 // status bits written by kernels
 constexpr int STATUS_NOCONV = 1;
 constexpr int STATUS_OVERFLOW = 2;
@@ -133,6 +168,14 @@ int launch_gemm_tf32x3(const TcGemmDesc* d, const long long* tile_prefix, int np
                        long long max_spin, int* err, void* stream);
 int launch_spmm_t_f32(const SpmmTDesc* d, const long long* prefix, int nprob, long long total, void* stream);
 int launch_extract_f32(const float* const* fin, int npairs, int ld, double* H, double* S, void* stream);
+int launch_slice_rows(const SliceRowsDesc* d, const long long* prefix, int n, long long rows, void* stream);
+int launch_slice_cols(const SliceColsDesc* d, const long long* prefix, int n, long long blocks, void* stream);
+int launch_slice_sites(const SliceSiteDesc* d, const long long* prefix, int n, long long rows, void* stream);
+int launch_spmm_df(const SpmmDfDesc* d, const long long* prefix, int n, long long total, void* stream);
+int launch_unit_env(float2* const* env, int n, void* stream);
+int launch_extract_df(const float2* const* fin, int npairs, double* H, double* S, void* stream);
+int launch_gemm_bf16s(const OzGemmDesc* d, const long long* tile_prefix, int nprob, long long total_tiles,
+                      long long max_spin, int* err, void* stream);
 int launch_solve(const double* d_H, const double* d_S, int M, double eps, int max_sweeps,
                  double* d_E, double* d_C, int* d_rank, double* d_kappa, int* d_status, void* stream);
 

@@ -1,0 +1,270 @@
+// Sliced-BF16 transfer contraction (tcgen05 GEMMs with exact leading-order
+// accumulation; see oz_gemm.cuh) with double-float environments.
+//
+// Per site and pair, environments L[a][w][b] are double-floats (hi, lo FP32):
+//   slice A   L rows (a,w) over b          -> BF16 slices + row exponents
+//   stage 1   X[(a,w)][(k',b')] = L . ketT               sliced tcgen05 GEMM
+//   stage 2   Y[(a,k)][(w',b')] = sum W X                double-float sparse MPO
+//   slice B   Y columns (w',b') over (a,k) -> BF16 slices (K-major, transposed)
+//   stage 3   L'[a'][(w',b')]   = braT . Yt              sliced tcgen05 GEMM
+// The site tensors (FP64) are sliced once per call: ketT rows (k',b') over b,
+// braT rows a' over (a,k).  Every value outside the tensor cores stays a
+// double-float (about 48 significant bits); the tensor cores see only exact
+// BF16 slices, so the contraction error is the slicing truncation alone.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include "internal.h"
+#define TNQE_DEFINE_OZ_KERNEL
+#include "oz_gemm.cuh"
+
+namespace tnqe {
+namespace {
+
+// Error-free transforms with explicit rounding (never contracted into FMAs).
+__device__ __forceinline__ void two_sum_rn(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+// (ah, al) += (vh, vl) * (xh, xl)
+__device__ __forceinline__ void df_fma(float vh, float vl, float xh, float xl, float& ah, float& al) {
+  const float p = __fmul_rn(vh, xh);
+  const float pe = __fadd_rn(fmaf(vh, xh, -p), __fadd_rn(__fmul_rn(vh, xl), __fmul_rn(vl, xh)));
+  float s, e;
+  two_sum_rn(ah, p, s, e);
+  ah = s;
+  al = __fadd_rn(al, __fadd_rn(e, pe));
+}
+__device__ __forceinline__ float2 df_norm(float h, float l) {
+  const float s = __fadd_rn(h, l);
+  return make_float2(s, __fsub_rn(l, __fsub_rn(s, h)));
+}
+__device__ __forceinline__ int find_prob(const long long* prefix, int nprob, long long x) {
+  int lo = 0, hi = nprob - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (prefix[mid] <= x) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+// row exponent e with max|x| 2^-e < 1/2 (0 for an all-zero row)
+__device__ __forceinline__ int row_exponent_f(float m) { return m > 0.f ? ilogbf(m) + 2 : 0; }
+__device__ __forceinline__ int row_exponent_d(double m) { return m > 0.0 ? ilogb(m) + 2 : 0; }
+
+// Slices of one double-float value x = hi + lo (|x| 2^-e < 1/2): out[i] = S_i 2^-(8(i+1)).
+__device__ __forceinline__ void slice_df(float hi, float lo, int e, int ns, __nv_bfloat16* out, long long stride) {
+  float th = ldexpf(hi, 8 - e), tl = ldexpf(lo, 8 - e);
+  for (int i = 0; i < ns; ++i) {
+    const float S = rintf(th);
+    float sh, sl;
+    two_sum_rn(__fsub_rn(th, S), tl, sh, sl);
+    out[i * stride] = __float2bfloat16_rn(ldexpf(S, -8 * (i + 1)));
+    th = __fmul_rn(sh, 256.f);
+    tl = __fmul_rn(sl, 256.f);
+  }
+}
+__device__ __forceinline__ void slice_d(double x, int e, int ns, __nv_bfloat16* out, long long stride) {
+  double t = ldexp(x, 8 - e);
+  for (int i = 0; i < ns; ++i) {
+    const double S = rint(t);
+    out[i * stride] = __float2bfloat16_rn(ldexpf((float)S, -8 * (i + 1)));
+    t = (t - S) * 256.0;
+  }
+}
+
+// One warp per row: df rows over K -> slices [ns][rows][ldK] and exponents.
+__global__ void __launch_bounds__(256) slice_rows_kernel(const SliceRowsDesc* __restrict__ descs,
+                                                         const long long* __restrict__ prefix, int nprob,
+                                                         long long total) {
+  const long long task = (long long)blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (task >= total) return;
+  const int lane = threadIdx.x & 31;
+  const int p = find_prob(prefix, nprob, task);
+  const SliceRowsDesc& d = descs[p];
+  const long long r = task - prefix[p];
+  const float2* src = d.src + r * d.ld;
+  float m = 0.f;
+  for (int k = lane; k < d.K; k += 32) m = fmaxf(m, fabsf(src[k].x));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  const int e = row_exponent_f(m);
+  if (lane == 0) d.exps[r] = e;
+  __nv_bfloat16* dst = d.dst + r * d.ldK;
+  for (int k = lane; k < d.K; k += 32) {
+    const float2 x = src[k];
+    slice_df(x.x, x.y, e, d.ns, dst + k, d.slice_stride);
+  }
+}
+
+// Columns (w',b') of Y[(a,k)][(w',b')] over K = (a,k), transposed to K-major slices.
+// One CTA per 16 columns of one problem; 256 threads.
+__global__ void __launch_bounds__(256) slice_cols_kernel(const SliceColsDesc* __restrict__ descs,
+                                                         const long long* __restrict__ prefix, int nprob) {
+  __shared__ float2 tile[64][17];
+  __shared__ float red[16][17];
+  __shared__ int sexp[16];
+  const long long task = blockIdx.x;
+  const int p = find_prob(prefix, nprob, task);
+  const SliceColsDesc& d = descs[p];
+  const int c0 = (int)(task - prefix[p]) * 16;
+  const int tid = threadIdx.x, cc = tid & 15, rr = tid >> 4;   // 16 columns x 16 row groups
+  const int col = c0 + cc;
+  float m = 0.f;
+  if (col < d.ncols)
+    for (int k = rr; k < d.K; k += 16) m = fmaxf(m, fabsf(d.src[(long long)k * d.ld + col].x));
+  red[rr][cc] = m;
+  __syncthreads();
+  if (tid < 16) {
+    float mm = 0.f;
+    for (int i = 0; i < 16; ++i) mm = fmaxf(mm, red[i][tid]);
+    const int e = row_exponent_f(mm);
+    sexp[tid] = e;
+    if (c0 + tid < d.ncols) d.exps[c0 + tid] = e;
+  }
+  __syncthreads();
+  // writer mapping: column wc = tid / 16, four consecutive k per thread
+  const int wc = tid >> 4, wk = (tid & 15) * 4;
+  for (int k0 = 0; k0 < d.K; k0 += 64) {
+    for (int i = tid; i < 64 * 16; i += 256) {
+      const int k = k0 + (i >> 4), c = c0 + (i & 15);
+      tile[i >> 4][i & 15] = (k < d.K && c < d.ncols) ? d.src[(long long)k * d.ld + c] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    if (c0 + wc < d.ncols) {
+      __nv_bfloat16* dst = d.dst + (long long)(c0 + wc) * d.ldK;
+      for (int u = 0; u < 4; ++u) {
+        const int k = k0 + wk + u;
+        if (k < d.K) slice_df(tile[wk + u][wc].x, tile[wk + u][wc].y, sexp[wc], d.ns, dst + k, d.slice_stride);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// FP64 site tensors -> K-major slices.  mode 0 (ket): rows (k',b') over b of
+// B[b][k'][b'];  mode 1 (bra): rows a' over (a,k) of A[a][k][a'].  Warp per row.
+__global__ void __launch_bounds__(256) slice_sites_kernel(const SliceSiteDesc* __restrict__ descs,
+                                                          const long long* __restrict__ prefix, int nprob,
+                                                          long long total) {
+  const long long task = (long long)blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (task >= total) return;
+  const int lane = threadIdx.x & 31;
+  const int p = find_prob(prefix, nprob, task);
+  const SliceSiteDesc& d = descs[p];
+  const int r = (int)(task - prefix[p]);
+  int K;
+  long long base, step;
+  if (d.mode == 0) {            // row (k', b'): element b at src[(b * 4 + k') * cr + b']
+    const int kp = r / d.cr, bp = r % d.cr;
+    K = d.cl;
+    base = (long long)kp * d.cr + bp;
+    step = 4LL * d.cr;
+  } else {                      // row a': element (a, k) at src[(a * 4 + k) * cr + a']
+    K = 4 * d.cl;
+    base = r;
+    step = d.cr;
+  }
+  double m = 0.0;
+  for (int k = lane; k < K; k += 32) m = fmax(m, fabs(d.src[base + k * step]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  const int e = row_exponent_d(m);
+  if (lane == 0) d.exps[r] = e;
+  __nv_bfloat16* dst = d.dst + (long long)r * d.ldK;
+  for (int k = lane; k < K; k += 32) slice_d(d.src[base + k * step], e, d.ns, dst + k, d.slice_stride);
+}
+
+// Y[a][row][0:width] = sum val * X[a][col][0:width], double-float; one warp per (a, row)
+__global__ void __launch_bounds__(256) spmm_df_kernel(const SpmmDfDesc* __restrict__ descs,
+                                                      const long long* __restrict__ prefix, int nprob,
+                                                      long long total) {
+  const long long task = (long long)blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (task >= total) return;
+  const int lane = threadIdx.x & 31;
+  const int p = find_prob(prefix, nprob, task);
+  const SpmmDfDesc& d = descs[p];
+  const long long local = task - prefix[p];
+  const int a = (int)(local / d.nrows), row = (int)(local % d.nrows);
+  const int e0 = d.rowptr[row], e1 = d.rowptr[row + 1];
+  const float2* Xa = d.X + (long long)a * d.ncols_x * d.width;
+  float2* y = d.Y + ((long long)a * d.nrows + row) * d.width;
+  for (int c0 = 0; c0 < d.width; c0 += 128) {
+    float ah[4] = {0.f, 0.f, 0.f, 0.f}, al[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int e = e0; e < e1; ++e) {
+      const float2 v = d.val[e];
+      const float2* x = Xa + (long long)d.col[e] * d.width;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int c = c0 + lane + 32 * u;
+        if (c < d.width) {
+          const float2 xv = x[c];
+          df_fma(v.x, v.y, xv.x, xv.y, ah[u], al[u]);
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int c = c0 + lane + 32 * u;
+      if (c < d.width) y[c] = df_norm(ah[u], al[u]);
+    }
+  }
+}
+
+__global__ void unit_env_kernel(float2* const* __restrict__ env, int n) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < n) env[p][0] = make_float2(1.f, 0.f);
+}
+
+__global__ void extract_df_kernel(const float2* const* __restrict__ fin, int npairs, double* H, double* S) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= npairs) return;
+  const float2 s = fin[p][0], h = fin[p][1];   // identity-string and completed-Hamiltonian channels
+  S[p] = (double)s.x + (double)s.y;
+  H[p] = (double)h.x + (double)h.y;
+}
+
+}  // namespace
+
+int launch_slice_rows(const SliceRowsDesc* d, const long long* prefix, int n, long long rows, void* stream) {
+  if (rows <= 0) return 0;
+  slice_rows_kernel<<<(unsigned)((rows + 7) / 8), 256, 0, (cudaStream_t)stream>>>(d, prefix, n, rows);
+  return (int)cudaGetLastError();
+}
+int launch_slice_cols(const SliceColsDesc* d, const long long* prefix, int n, long long blocks, void* stream) {
+  if (blocks <= 0) return 0;
+  slice_cols_kernel<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(d, prefix, n);
+  return (int)cudaGetLastError();
+}
+int launch_slice_sites(const SliceSiteDesc* d, const long long* prefix, int n, long long rows, void* stream) {
+  if (rows <= 0) return 0;
+  slice_sites_kernel<<<(unsigned)((rows + 7) / 8), 256, 0, (cudaStream_t)stream>>>(d, prefix, n, rows);
+  return (int)cudaGetLastError();
+}
+int launch_spmm_df(const SpmmDfDesc* d, const long long* prefix, int n, long long total, void* stream) {
+  if (total <= 0) return 0;
+  spmm_df_kernel<<<(unsigned)((total + 7) / 8), 256, 0, (cudaStream_t)stream>>>(d, prefix, n, total);
+  return (int)cudaGetLastError();
+}
+int launch_unit_env(float2* const* env, int n, void* stream) {
+  if (n <= 0) return 0;
+  unit_env_kernel<<<(n + 127) / 128, 128, 0, (cudaStream_t)stream>>>(env, n);
+  return (int)cudaGetLastError();
+}
+int launch_extract_df(const float2* const* fin, int npairs, double* H, double* S, void* stream) {
+  if (npairs <= 0) return 0;
+  extract_df_kernel<<<(npairs + 127) / 128, 128, 0, (cudaStream_t)stream>>>(fin, npairs, H, S);
+  return (int)cudaGetLastError();
+}
+int launch_gemm_bf16s(const OzGemmDesc* d, const long long* tile_prefix, int nprob, long long total_tiles,
+                      long long max_spin, int* err, void* stream) {
+  if (total_tiles <= 0) return 0;
+  const cudaError_t e =
+      cudaFuncSetAttribute(gemm_bf16s_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM_BYTES);
+  if (e != cudaSuccess) return (int)e;
+  gemm_bf16s_kernel<<<(unsigned)total_tiles, OZ_THREADS, OZ_SMEM_BYTES, (cudaStream_t)stream>>>(d, tile_prefix, nprob,
+                                                                                               max_spin, err);
+  return (int)cudaGetLastError();
+}
+
+}  // namespace tnqe

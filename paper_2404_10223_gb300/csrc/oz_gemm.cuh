@@ -1,0 +1,311 @@
+// Sliced-BF16 grouped GEMM on the 5th-generation tensor cores (sm_103a).
+//
+// Both operands arrive as fixed-point BF16 slices (error-free splitting in the
+// manner of Ozaki, Ogita, Oishi and Rump, Numer. Algorithms 59 (2012) 95):
+// row r of an operand, scaled by 2^-e_r so that every entry is below 1/2 in
+// magnitude, is written as x' = v_1 + v_2 + ... + v_S with
+// v_i = S_i 2^(-8 i), S_i an integer in [-128, 128].  Every v_i is exact in
+// BF16, every slice product v_i^A v_j^B is exact in FP32, and the sums
+//   acc0 = sum_k v_1^A v_1^B      (multiples of 2^-16, |.| <= K 2^-2)
+//   acc1 = sum_k v_1^A v_2^B      (multiples of 2^-24, |.| <= K 2^-9)
+//   acc2 = sum_k v_2^A v_1^B
+// stay exact in FP32 for K <= 1024, so the three leading orders carry no
+// rounding at all; acc3 collects the orders i + j = 4, 5 (at most 2^-16 of the
+// leading term) with ordinary FP32 rounding.  The epilogue adds the four
+// accumulators error-free into a double-float (hi + lo, two FP32 values) and
+// scales by 2^(e_r + e_c).
+//
+// One CTA computes one 128 x 128 tile of one problem: thread 0 issues the TMA
+// loads (3-D boxes: 32 K-elements x 128 rows x S slices, 64-byte swizzle) and
+// the tcgen05.mma instructions; the four accumulators fill the 512 columns of
+// tensor memory; all four warps run the epilogue.
+#pragma once
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace tnqe {
+
+constexpr int OZ_BM = 128, OZ_BN = 128, OZ_BK = 32;    // BK in BF16 elements (64 bytes)
+constexpr int OZ_MAXS = 5;                             // slices per operand
+constexpr int OZ_MAXK = 1024;                          // exactness bound of acc0..acc2
+constexpr int OZ_THREADS = 128;
+constexpr int OZ_SLICE_BYTES = OZ_BM * OZ_BK * 2;      // 8 KiB per slice tile
+constexpr int OZ_MAX_STAGES = 4;
+constexpr int OZ_STAGE_AREA = 196608;                  // pipeline stages: 2 S slice tiles each
+constexpr int OZ_GUARD = 16384;                        // slack after the stage area
+constexpr int OZ_SMEM_BYTES = OZ_STAGE_AREA + OZ_GUARD + 1024 /*align*/ + 256 /*barriers*/;
+constexpr int OZ_TMEM_COLS = 512;
+// pipeline depth for S slices: as many stages of 2 S tiles as fit the stage area
+__host__ __device__ constexpr int oz_stages(int S) {
+  return (OZ_STAGE_AREA / (2 * S * OZ_SLICE_BYTES)) < OZ_MAX_STAGES ? (OZ_STAGE_AREA / (2 * S * OZ_SLICE_BYTES))
+                                                                    : OZ_MAX_STAGES;
+}
+
+struct OzGemmDesc {     // CUtensorMap members carry the required alignment
+  CUtensorMap mapA;     // dims {K, M, S}: slice s of row m at A + (s * M + m) * ldK, box {32, 128, S}
+  CUtensorMap mapB;     // dims {K, N, S}
+  const int* ea;        // M row exponents of A
+  const int* eb;        // N row exponents of B
+  float2* C;            // element (m, n) at C + m * ldc + (n / cg) * cld + n % cg, as (hi, lo)
+  long long ldc;
+  int M, N, K;
+  int cg, cld;
+  int tiles_n;
+  int nslices;          // 2 .. 5
+  int pad;
+};
+
+#if defined(__CUDACC__) && defined(TNQE_DEFINE_OZ_KERNEL)
+namespace ozdev {
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ uint32_t mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok;
+}
+// Bounded wait on an mbarrier phase; false if the limit ran out.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long long limit) {
+  for (long long i = 0; i < limit; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y, int z) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], "
+      "[%2];" ::"r"(smem_u32(dst)),
+      "l"(map), "r"(smem_u32(bar)), "r"(x), "r"(y), "r"(z)
+      : "memory");
+}
+__device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)),
+               "r"(ncols)
+               : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accum) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+          d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+// 16 consecutive accumulator columns of this thread's TMEM lane
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+        "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// K-major operand tile, 64-byte swizzle: 64-byte rows, 8-row groups 512 bytes apart
+__device__ __forceinline__ uint64_t sw64_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)1 << 16;            // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(512 >> 4) << 32;   // stride byte offset: next 8-row group
+  d |= (uint64_t)1 << 46;            // descriptor version
+  d |= (uint64_t)4 << 61;            // SWIZZLE_64B
+  return d;
+}
+// kind::f16 with BF16 A and B, FP32 accumulator, both K-major, M = 128, N = 128
+constexpr uint32_t OZ_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(OZ_BN >> 3) << 17) |
+                              ((uint32_t)(OZ_BM >> 4) << 24);
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+// 2^e as a float for -126 <= e <= 127
+__device__ __forceinline__ float pow2f(int e) {
+  e = max(-126, min(127, e));
+  return __int_as_float((e + 127) << 23);
+}
+
+}  // namespace ozdev
+
+constexpr int OZ_ERR_TIMEOUT = 1;
+
+__global__ void __launch_bounds__(OZ_THREADS, 1)
+    gemm_bf16s_kernel(const OzGemmDesc* __restrict__ descs, const long long* __restrict__ tile_prefix, int nprob,
+                      long long max_spin, int* __restrict__ err) {
+  using namespace ozdev;
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + OZ_STAGE_AREA + OZ_GUARD);
+  uint64_t* empty = full + OZ_MAX_STAGES;
+  uint64_t* accb = empty + OZ_MAX_STAGES;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accb + 1);
+  __shared__ int s_fail;
+
+  const long long tile = blockIdx.x;
+  int lo = 0, hi = nprob - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (tile_prefix[mid] <= tile) lo = mid; else hi = mid - 1;
+  }
+  const OzGemmDesc* d = descs + lo;
+  const long long local = tile - tile_prefix[lo];
+  const int tm = (int)(local / d->tiles_n), tn = (int)(local % d->tiles_n);
+  const int m0 = tm * OZ_BM, n0 = tn * OZ_BN;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int KT = (d->K + OZ_BK - 1) / OZ_BK;
+  const int S = d->nslices;
+  const int NST = oz_stages(S);
+  const int stage_bytes = 2 * S * OZ_SLICE_BYTES;
+
+  if (tid == 0) {
+    s_fail = 0;
+    for (int s = 0; s < OZ_MAX_STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(accb, 1);
+    fence_mbar_init();
+  }
+  if (warp == 0) {
+    tmem_alloc(tmem_slot, OZ_TMEM_COLS);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  int fail = 0;
+  if (tid == 0) {
+    const uint32_t tx = (uint32_t)(2 * S * OZ_SLICE_BYTES);
+    auto stage_a = [&](int s) { return smem + s * stage_bytes; };
+    auto stage_b = [&](int s) { return smem + s * stage_bytes + S * OZ_SLICE_BYTES; };
+    auto issue = [&](int s, int kt) {
+      mbar_expect_tx(&full[s], tx);
+      tma_load_3d(stage_a(s), &d->mapA, &full[s], kt * OZ_BK, m0, 0);
+      tma_load_3d(stage_b(s), &d->mapB, &full[s], kt * OZ_BK, n0, 0);
+    };
+    int issued = 0, consumed = 0;
+    for (int s = 0; s < NST && s < KT; ++s, ++issued) issue(s, s);
+    bool started3 = false;
+    for (int kt = 0; kt < KT && !fail; ++kt) {
+      const int s = kt % NST;
+      if (!mbar_wait(&full[s], (uint32_t)((kt / NST) & 1), max_spin)) {
+        fail = 1;
+        break;
+      }
+      consumed = kt + 1;
+      tc_fence_after();
+      const uint32_t a0 = smem_u32(stage_a(s)), b0 = smem_u32(stage_b(s));
+#pragma unroll
+      for (int k = 0; k < OZ_BK / 16; ++k) {        // 16 BF16 = 32 bytes per MMA along K
+        const uint32_t acc_on = (kt > 0 || k > 0) ? 1u : 0u;
+        auto da = [&](int i) { return sw64_desc(a0 + i * OZ_SLICE_BYTES + 32 * k); };
+        auto db = [&](int j) { return sw64_desc(b0 + j * OZ_SLICE_BYTES + 32 * k); };
+        mma_bf16(tmem + 0 * OZ_BN, da(0), db(0), OZ_IDESC, acc_on);
+        mma_bf16(tmem + 1 * OZ_BN, da(0), db(1), OZ_IDESC, acc_on);
+        mma_bf16(tmem + 2 * OZ_BN, da(1), db(0), OZ_IDESC, acc_on);
+        // orders 4 .. S + 1 into acc3 (0-based slice indices i + j = 2 .. S - 1)
+        for (int i = 0; i < S; ++i)
+          for (int j = 0; j < S; ++j) {
+            const int ord = i + j;
+            if (ord < 2 || ord > S - 1) continue;
+            mma_bf16(tmem + 3 * OZ_BN, da(i), db(j), OZ_IDESC, started3 ? 1u : 0u);
+            started3 = true;
+          }
+      }
+      mma_commit(&empty[s]);
+      // refill the stage read by the previous k-tile once its MMAs are done
+      if (kt >= 1 && kt - 1 + NST < KT) {
+        const int sp = (kt - 1) % NST;
+        if (!mbar_wait(&empty[sp], (uint32_t)(((kt - 1) / NST) & 1), max_spin)) {
+          fail = 1;
+          break;
+        }
+        issue(sp, kt - 1 + NST);
+        ++issued;
+      }
+    }
+    mma_commit(accb);   // arrives once every issued MMA is done, also after a failure
+    if (fail)           // let the loads still in flight land before the CTA leaves
+      for (int q = consumed; q < issued; ++q) mbar_wait(&full[q % NST], (uint32_t)((q / NST) & 1), max_spin);
+  }
+  if (!mbar_wait(accb, 0, max_spin)) fail = 1;
+  tc_fence_after();
+  if (fail) {
+    s_fail = 1;
+    atomicExch(err, OZ_ERR_TIMEOUT);
+  }
+  __syncthreads();
+  if (!s_fail) {
+    const int row = m0 + warp * 32 + lane;
+    const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+    const bool has3 = S >= 3;
+    const int era = row < d->M ? d->ea[row] : 0;
+#pragma unroll 1
+    for (int c0 = 0; c0 < OZ_BN; c0 += 16) {
+      uint32_t v0[16], v1[16], v2[16], v3[16];
+      tmem_ld16(lane_base + 0 * OZ_BN + c0, v0);
+      tmem_ld16(lane_base + 1 * OZ_BN + c0, v1);
+      tmem_ld16(lane_base + 2 * OZ_BN + c0, v2);
+      tmem_ld16(lane_base + 3 * OZ_BN + c0, v3);
+      tmem_wait_ld();
+      if (row < d->M) {
+        float2* crow = d->C + (long long)row * d->ldc;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int n = n0 + c0 + j;
+          if (n >= d->N) continue;
+          float s, e, e2;
+          two_sum(__uint_as_float(v0[j]), __uint_as_float(v1[j]), s, e);
+          two_sum(s, __uint_as_float(v2[j]), s, e2);
+          e += e2;
+          if (has3) e += __uint_as_float(v3[j]);
+          const float h = s + e;
+          const float l = e - (h - s);
+          const int ex = era + d->eb[n];
+          const float s1 = pow2f(ex / 2), s2 = pow2f(ex - ex / 2);
+          crow[(long long)(n / d->cg) * d->cld + (n % d->cg)] = make_float2(h * s1 * s2, l * s1 * s2);
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    tmem_dealloc(tmem, OZ_TMEM_COLS);
+  }
+}
+#endif
+
+}  // namespace tnqe

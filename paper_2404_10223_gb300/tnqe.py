@@ -18,7 +18,8 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libtnqe.so")
 
-TNQE_PREC_FP64, TNQE_PREC_TF32X3, TNQE_PREC_BF16X3 = 0, 1, 2
+TNQE_PREC_FP64, TNQE_PREC_TF32X3, TNQE_PREC_BF16X3, TNQE_PREC_BF16X6, TNQE_PREC_BF16X10, TNQE_PREC_BF16X15 = range(6)
+TNQE_PROFILE_LEN = 12
 STATUS_NAMES = {0: "TNQE_OK", 1: "TNQE_ERR_ARG", 2: "TNQE_ERR_STATE", 3: "TNQE_ERR_NOMEM", 4: "TNQE_ERR_CUDA",
                 5: "TNQE_ERR_NOCONV", 6: "TNQE_ERR_TIMEOUT", 7: "TNQE_ERR_NUMERIC"}
 
@@ -175,8 +176,8 @@ def tnqe_last_timing(ctx):
 
 
 def tnqe_last_profile(ctx) -> np.ndarray:
-    p = np.zeros(10)
-    _check(ctx, load().tnqe_last_profile(ctx, _ptr(p), 10))
+    p = np.zeros(TNQE_PROFILE_LEN)
+    _check(ctx, load().tnqe_last_profile(ctx, _ptr(p), TNQE_PROFILE_LEN))
     return p
 
 

@@ -295,3 +295,67 @@ def test_tf32x3_contraction_error_against_fp64():
     assert abs(E1[0] - E0[0]) <= 1e-4
     off = [k for k, (i, j) in enumerate(pairs) if i != j]
     assert np.abs(H1[off] - H0[off]).max() <= 1e-5
+
+
+# Measured on n10_chi32 against the FP64 path (max|dH|, max|dS|, |dE|):
+#   BF16X3 1.2e-2 / 4.5e-4 / 1.5e-2     BF16X6  8.6e-6 / 3.4e-7 / 1.1e-5
+#   BF16X10 1.7e-7 / 6.7e-9 / 1.8e-7    BF16X15 4.6e-9 / 2.5e-10 / 7.6e-9
+# The bounds below keep a margin of about five over those numbers.
+SLICED_BOUNDS = {
+    tnqe.TNQE_PREC_BF16X3: (5e-2, 2e-3, 5e-2),
+    tnqe.TNQE_PREC_BF16X6: (5e-5, 2e-6, 5e-5),
+    tnqe.TNQE_PREC_BF16X10: (1e-6, 5e-8, 1e-6),
+    tnqe.TNQE_PREC_BF16X15: (3e-8, 2e-9, 5e-8),
+}
+
+
+def test_sliced_bf16_contraction_errors_against_fp64():
+    """Sliced-BF16 tensor-core contractions: every mode's error stated and bounded."""
+    w = inputs.workload("n10_chi32")
+    pairs = w.all_pairs()
+    with gpu_ctx(w) as g:
+        H0, S0 = g.matrix_elements(pairs)
+        E0 = g.solve(*assemble(w.M, pairs, H0, S0))[0]
+        for prec, (bh, bs, be) in SLICED_BOUNDS.items():
+            g.set_precision(prec)
+            Hv, Sv = g.matrix_elements(pairs)
+            E = g.solve(*assemble(w.M, pairs, Hv, Sv))[0]
+            assert np.abs(Hv - H0).max() <= bh, (prec, np.abs(Hv - H0).max())
+            assert np.abs(Sv - S0).max() <= bs, (prec, np.abs(Sv - S0).max())
+            assert abs(E[0] - E0[0]) <= be, (prec, abs(E[0] - E0[0]))
+
+
+def test_sliced_bf16x15_against_exact_fock_n6():
+    """The most accurate sliced mode against the dense Fock-space oracle (lossless rotations)."""
+    w = inputs.workload("n6_chi8")
+    pairs = w.all_pairs()
+    Hf, Sf = of.matrix_elements(w.h1, w.eri, 3, 3, [m.tensors for m in w.mps], [m.U for m in w.mps], pairs)
+    with gpu_ctx(w, chi_rot=64, precision=tnqe.TNQE_PREC_BF16X15) as g:
+        Hv, Sv = g.matrix_elements(pairs)
+    assert np.abs(Hv - Hf).max() <= 1e-8
+    assert np.abs(Sv - Sf).max() <= 1e-9
+
+
+def test_sliced_bf16_ragged_and_tiny_chains():
+    """Ragged bond dimensions (tile tails in every GEMM) and N = 1, 2 chains in the sliced mode."""
+    for name in ("n14_mixed",):
+        w = inputs.workload(name)
+        allp = w.all_pairs()
+        pairs = [allp[k] for k in range(0, len(allp), 17)]
+        with gpu_ctx(w) as g:
+            H0, S0 = g.matrix_elements(pairs)
+            g.set_precision(tnqe.TNQE_PREC_BF16X15)
+            H1, S1 = g.matrix_elements(pairs)
+        assert np.abs(H1 - H0).max() <= 3e-7
+        assert np.abs(S1 - S0).max() <= 1e-8
+    for N, na, nb in [(1, 1, 0), (2, 1, 1), (3, 2, 1)]:
+        rng = np.random.default_rng(N)
+        h1, eri = inputs.draw_integrals(rng, N, 2)
+        states = [inputs.draw_mps(rng, N, na, nb, 4)[0] for _ in range(2)]
+        Us = [np.eye(N), inputs.draw_rotation(rng, N, 0.7)[1]]
+        HA, SA = of.matrix_elements(h1, eri, na, nb, states, Us, [(0, 0), (0, 1), (1, 1)])
+        with tnqe.Context(h1, eri, N, na, nb, chi_rot=64, precision=tnqe.TNQE_PREC_BF16X15) as g:
+            for t, U in zip(states, Us):
+                g.add_mps(t, U)
+            HG, SG = g.matrix_elements([(0, 0), (0, 1), (1, 1)])
+        assert np.abs(HG - HA).max() <= 1e-9 and np.abs(SG - SA).max() <= 1e-10
