@@ -78,10 +78,12 @@ typedef struct {
   long long max_spin;       /* iteration limit of any device-side wait */
   void* cuda_stream;        /* cudaStream_t to launch on; NULL = a stream owned by the context */
   int device;               /* CUDA device ordinal */
+  int use_graphs;           /* 1: replay repeated tnqe_matrix_elements calls from a captured CUDA graph */
 } tnqe_options;
 
 /* Fill *opt with defaults: FP64, chi_rot 0, cutoff 1e-14, solve_eps 1e-10,
- * no renormalisation, 60 Jacobi sweeps, max_spin 1<<26, own stream, device 0. */
+ * no renormalisation, 60 Jacobi sweeps, max_spin 1<<26, own stream, device 0,
+ * graphs on. */
 void tnqe_default_options(tnqe_options* opt);
 
 /* Create a context for N spatial orbitals and (n_alpha, n_beta) electrons.
@@ -119,9 +121,43 @@ tnqe_status tnqe_get_rotated(tnqe_ctx* ctx, int* bond_dims, double* tensors, lon
 
 /* H_ij and S_ij (Eq. 10) for npairs pairs.  pairs: 2*npairs ints (host),
  * (i, j) with i <= j.  H_out, S_out: npairs doubles each, host or device.
- * Every pair is recomputed (rotation and contraction) on each call. */
+ * Every pair is recomputed (rotation and contraction) on each call.
+ *
+ * One call puts all pairs' rotations (one launch) and contractions (a few
+ * launches per site, every pair batched in each) on the stream without any
+ * host synchronisation in between: rotated states are written at their bond
+ * capacities min(chi_rot, full sector dimension), zero-padded, so the
+ * contraction is planned before the truncation has run.  With use_graphs set,
+ * the second call for a (pair list, states, options) combination also captures
+ * that launch sequence into a CUDA graph; later identical calls replay it
+ * (re-uploading their descriptors, then one cudaGraphLaunch).  Adding or
+ * resetting states, changing options, or any workspace reallocation drops the
+ * graphs.  If the workspace of all pairs does not fit in 60% of free device
+ * memory the pairs run in waves, synchronised between waves, and are not
+ * captured. */
 tnqe_status tnqe_matrix_elements(tnqe_ctx* ctx, const int* pairs, int npairs,
                                  double* H_out, double* S_out);
+
+/* Launch-shape autotuner of the sliced-BF16 contraction (BF16X* precisions;
+ * a no-op otherwise).  Times the given pair list -- normally the one that
+ * will be computed repeatedly -- under three candidate shapes (stage-1 and
+ * stage-3 GEMM N tiles of 128 or 64 columns, MPO kernel widths of 8, 4 and 2
+ * ket columns per CTA), keeps for each kernel the shape with the smallest
+ * summed device time, and drops captured graphs.  Each candidate runs twice
+ * (the first run warms allocations).  config (3 ints, may be NULL) gets the
+ * chosen (bn1, bn3, spmm_bw); times (9 doubles, may be NULL) gets the
+ * per-candidate stage-1, stage-3 and MPO milliseconds. */
+tnqe_status tnqe_autotune(tnqe_ctx* ctx, const int* pairs, int npairs, int* config, double* times);
+
+/* Set the launch shapes directly: bn1, bn3 in {64, 128}; spmm_bw in
+ * {0 (largest that fits), 1, 2, 4, 8}. */
+tnqe_status tnqe_set_tuning(tnqe_ctx* ctx, int bn1, int bn3, int spmm_bw);
+
+/* Drop every captured graph of the context. */
+tnqe_status tnqe_clear_graphs(tnqe_ctx* ctx);
+
+/* Number of captured graphs the context holds (0 for NULL). */
+int tnqe_graph_count(const tnqe_ctx* ctx);
 
 /* Generalized eigenproblem H c = E S c (Eq. 9) for M <= 32 by canonical
  * orthogonalisation (projection method, Sec. IV C), on the GPU in FP64.

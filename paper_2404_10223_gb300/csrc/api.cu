@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -41,6 +43,10 @@ struct Error : std::runtime_error {
     if (e_ != 0) throw Error(TNQE_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString((cudaError_t)e_)); \
   } while (0)
 
+// Bumped by every (re)allocation of a workspace buffer: a captured CUDA graph
+// holds raw workspace addresses and is only replayed while this is unchanged.
+std::atomic<unsigned long long> g_alloc_epoch{0};
+
 // device allocation that grows on demand and is kept for reuse
 struct DBuf {
   void* p = nullptr;
@@ -53,6 +59,7 @@ struct DBuf {
     size_t b = std::max<size_t>(bytes, 256);
     CK(cudaMalloc(&p, b));
     cap = b;
+    ++g_alloc_epoch;
   }
   void release() {
     if (p) cudaFree(p);
@@ -88,7 +95,7 @@ struct DevMps {
   int* d_dims = nullptr;
   SectorTable* d_sec = nullptr;
   Mpo mpo;                               // host copy (dims, CSR)
-  std::vector<int*> d_rowptr, d_col;
+  std::vector<int*> d_rowptr, d_col, d_rowperm;
   std::vector<double*> d_val;
   std::vector<float*> d_val32;
   std::vector<float2*> d_valdf;          // (hi, lo) FP32 pairs of the MPO values
@@ -105,6 +112,34 @@ struct PairPlan {                        // cached per (i, j): Givens gates on t
   int* d_site = nullptr;
   int* d_side = nullptr;
   std::vector<void*> owned;
+};
+
+// A host-to-device copy that a graph replay repeats before launching the graph.
+struct Upload {
+  void* dst;
+  std::vector<unsigned char> data;
+};
+
+// What the host reads back after the work of one matrix-element call has run.
+struct FinishInfo {
+  const unsigned char* rot_small = nullptr;   // per-pair status / FLOP records of the rotation
+  size_t per_small = 0, o_stat = 0, o_flops = 0;
+  int nrot = 0;
+  std::vector<std::array<int, 3>> ev_reads;   // (event a, event b, profile slot): slot += elapsed(a, b)
+  std::vector<double> pstat;                  // profile values known at planning time
+  int launches = 0;
+  bool check_err = false;
+  bool single_wave = true;
+};
+
+struct GraphEntry {
+  cudaGraphExec_t exec = nullptr;
+  std::vector<Upload> uploads;
+  unsigned long long epoch = 0;
+  FinishInfo fin;
+  ~GraphEntry() {
+    if (exec) cudaGraphExecDestroy(exec);
+  }
 };
 
 }  // namespace
@@ -125,6 +160,16 @@ struct tnqe_ctx {
   DBuf con_ws, con_desc, con_out;
   DBuf tc_ws, tc_desc, tc_err;
   DBuf oz_ws, oz_desc;
+  // graph capture / replay of whole matrix-element calls
+  bool capturing = false;
+  std::vector<Upload>* cap_uploads = nullptr;
+  std::map<std::vector<long long>, std::unique_ptr<GraphEntry>> graphs;
+  std::map<std::vector<long long>, int> seen;   // calls per key: the second identical call captures
+  long long generation = 0;                // bumped whenever the set of states changes
+  // launch shapes (tnqe_autotune): sliced GEMM N tiles of stages 1 and 3, MPO kernel width (0 = largest that fits)
+  struct Tune {
+    int oz_bn1 = 128, oz_bn3 = 128, spmm_bw = 0;
+  } tune;
   // last tnqe_rotate result
   int kept_pair_valid = 0;
   std::vector<int> kept_dims;
@@ -153,6 +198,31 @@ bool is_device_ptr(const void* p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// Host-to-device copy of planning data.  While a call is being captured the
+// copy is recorded for the replays instead (each replay repeats it before the
+// graph launch), so the graph itself holds kernels only.
+void upload(tnqe_ctx* c, void* dst, const void* src, size_t n) {
+  if (n == 0) return;
+  if (c->capturing) {
+    const unsigned char* b = static_cast<const unsigned char*>(src);
+    c->cap_uploads->push_back(Upload{dst, std::vector<unsigned char>(b, b + n)});
+    return;
+  }
+  CK(cudaMemcpyAsync(dst, src, n, cudaMemcpyHostToDevice, c->stream));
+}
+
+// Event on the context stream; while capturing, an event-record node of the graph
+// (a plain record inside a capture only orders work and is not replayed).
+void record_event(tnqe_ctx* c, cudaEvent_t e) {
+  if (c->capturing) CK(cudaEventRecordWithFlags(e, c->stream, cudaEventRecordExternal));
+  else CK(cudaEventRecord(e, c->stream));
+}
+
+void clear_graphs(tnqe_ctx* c) {
+  c->graphs.clear();
+  c->seen.clear();
+}
+
 // ----------------------------------------------------------------------------- rotation of a batch
 struct RotBatch {
   std::vector<int> pair_idx;             // index into the caller's pair list
@@ -169,6 +239,7 @@ struct RotBatch {
   std::vector<double*> disc;
   std::vector<int*> status;
   std::vector<double*> flops;
+  size_t per_small = 0, o_stat = 0, o_flops = 0;
 };
 
 const long long META_INTS = 2 * 32768;
@@ -209,7 +280,7 @@ PairPlan* get_plan(tnqe_ctx* c, int i, int j) {
 int chi_rot_of(tnqe_ctx* c, int j) { return c->opt.chi_rot > 0 ? c->opt.chi_rot : c->mps[j]->chi; }
 
 // Launch the rotation of every (i, j), i != j, of `pairs`; results stay in rot_work.
-void run_rotations(tnqe_ctx* c, const std::vector<std::pair<int, int>>& pairs, RotBatch& rb) {
+void run_rotations(tnqe_ctx* c, const std::vector<std::pair<int, int>>& pairs, RotBatch& rb, int pad_out) {
   const int N = c->N;
   rb = RotBatch{};
   for (size_t p = 0; p < pairs.size(); ++p)
@@ -236,6 +307,7 @@ void run_rotations(tnqe_ctx* c, const std::vector<std::pair<int, int>>& pairs, R
     }
     long long th = 16;
     for (int a = 0; a + 1 < N; ++a) th = std::max(th, 16LL * cap[a] * cap[a + 2]);
+    for (int a = 0; a < N; ++a) th = std::max(th, 4LL * cap[a] * cap[a + 1]);   // one site at capacity
     rb.cap.push_back(cap);
     rb.woff.push_back(off);
     rb.work_base.push_back(work_total);
@@ -271,8 +343,10 @@ void run_rotations(tnqe_ctx* c, const std::vector<std::pair<int, int>>& pairs, R
     o += (size_t)(N + 1) * 8 * 2 + (size_t)N * 8;
     double* ddisc = reinterpret_cast<double*>(db + o);
     double* dflops = reinterpret_cast<double*>(db + o + 8);
+    rb.o_flops = o + 8;
     o += 16;
     int* dstat = reinterpret_cast<int*>(db + o);
+    rb.o_stat = o;
     const DevMps& mj = *c->mps[rb.jj[k]];
     PairPlan* pl = get_plan(c, rb.ii[k], rb.jj[k]);
     RotDesc& d = descs[k];
@@ -281,6 +355,7 @@ void run_rotations(tnqe_ctx* c, const std::vector<std::pair<int, int>>& pairs, R
     d.ngates = pl->ngates;
     d.neg_site = pl->neg_site;
     d.renorm = c->opt.renormalize_rotated;
+    d.pad_out = pad_out;
     d.max_sweeps = c->opt.max_jacobi_sweeps;
     d.cutoff = c->opt.cutoff;
     d.src = mj.d_t;
@@ -316,11 +391,12 @@ void run_rotations(tnqe_ctx* c, const std::vector<std::pair<int, int>>& pairs, R
     rb.status.push_back(dstat);
     rb.flops.push_back(dflops);
   }
-  CK(cudaMemcpyAsync(c->rot_small.p, small.data(), small.size(), cudaMemcpyHostToDevice, c->stream));
-  CK(cudaMemcpyAsync(c->rot_desc.p, descs.data(), sizeof(RotDesc) * np, cudaMemcpyHostToDevice, c->stream));
-  CK(cudaEventRecord(c->pev[0], c->stream));
+  rb.per_small = per_small;
+  upload(c, c->rot_small.p, small.data(), small.size());
+  upload(c, c->rot_desc.p, descs.data(), sizeof(RotDesc) * np);
+  record_event(c, c->pev[0]);
   CKL(launch_rotate(c->rot_desc.as<RotDesc>(), np, 0, c->stream));
-  CK(cudaEventRecord(c->pev[1], c->stream));
+  record_event(c, c->pev[1]);
   c->launches += 1;
 }
 
@@ -359,8 +435,25 @@ struct KetView {
   std::vector<int> dims;        // N + 1
 };
 
+// Per-site event pairs of the last wave go to the finish step; earlier waves
+// (which reuse the workspace) are synchronised and read here.
+void site_events(tnqe_ctx* c, FinishInfo& fi, bool last, const std::vector<std::array<int, 3>>& reads) {
+  if (last) {
+    fi.ev_reads.insert(fi.ev_reads.end(), reads.begin(), reads.end());
+    return;
+  }
+  if (c->capturing) throw Error(TNQE_ERR_STATE, "a captured call must fit one workspace wave");
+  fi.single_wave = false;
+  CK(cudaStreamSynchronize(c->stream));
+  for (const auto& r : reads) {
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, c->pev[r[0]], c->pev[r[1]]));
+    c->prof[r[2]] += ms;
+  }
+}
+
 void run_contractions(tnqe_ctx* c, const std::vector<std::pair<int, int>>& pairs, const std::vector<KetView>& kets,
-                      double* d_H, double* d_S) {
+                      double* d_H, double* d_S, FinishInfo& fi) {
   const int N = c->N;
   const int np = (int)pairs.size();
   // workspace per pair: two environments, X and Y
@@ -484,10 +577,11 @@ void run_contractions(tnqe_ctx* c, const std::vector<std::pair<int, int>>& pairs
     const size_t bp1 = g1pre.size() * 8, bp3 = g3pre.size() * 8, bps = sppre.size() * 8;
     const size_t bf = (size_t)nw * sizeof(double*);
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
-    const size_t total = al(b1) + al(b3) + al(bs) + al(bp1) + al(bp3) + al(bps) + al(bf);
+    const size_t total = al(b1) + al(b3) + al(bs) + al(bp1) + al(bp3) + al(bps) + al(bf) + al(bf);
     std::vector<unsigned char> host(total, 0);
     size_t o1 = 0, o3 = o1 + al(b1), os = o3 + al(b3), op1 = os + al(bs), op3 = op1 + al(bp1), ops = op3 + al(bp3),
-           of = ops + al(bps);
+           of = ops + al(bps), oe = of + al(bf);
+    std::memcpy(host.data() + oe, env0.data(), bf);
     std::memcpy(host.data() + o1, g1.data(), b1);
     std::memcpy(host.data() + o3, g3.data(), b3);
     std::memcpy(host.data() + os, sp.data(), bs);
@@ -499,13 +593,9 @@ void run_contractions(tnqe_ctx* c, const std::vector<std::pair<int, int>>& pairs
     std::memcpy(host.data() + of, fin.data(), bf);
     c->con_desc.ensure(total);
     unsigned char* dd = c->con_desc.as<unsigned char>();
-    CK(cudaMemcpyAsync(dd, host.data(), total, cudaMemcpyHostToDevice, c->stream));
-    // L_0 = 1 for every pair of the wave
-    {
-      const double one = 1.0;
-      for (int w = 0; w < nw; ++w)
-        CK(cudaMemcpyAsync(env0[w], &one, sizeof(double), cudaMemcpyHostToDevice, c->stream));
-    }
+    upload(c, dd, host.data(), total);
+    CKL(launch_unit_env_f64(reinterpret_cast<double* const*>(dd + oe), nw, c->stream));   // L_0 = 1
+    c->launches += 1;
     for (const GemmDesc& d : g1) c->prof[5] += 2.0 * d.M * d.N * d.K;
     for (const GemmDesc& d : g3) c->prof[7] += 2.0 * d.M * d.N * d.K;
     for (int w = 0; w < nw; ++w) {
@@ -522,16 +612,16 @@ void run_contractions(tnqe_ctx* c, const std::vector<std::pair<int, int>>& pairs
     for (int t = 0; t < N; ++t) {
       const int n1 = g1n[t], n3 = g3n[t], ns = spn[t];
       cudaEvent_t* E = &c->pev[2 + 6 * t];
-      CK(cudaEventRecord(E[0], c->stream));
+      record_event(c, E[0]);
       CKL(launch_gemm_f64(reinterpret_cast<GemmDesc*>(dd + o1) + i1, reinterpret_cast<long long*>(dd + op1) + ip1,
                           n1, g1pre[ip1 + n1], c->stream));
-      CK(cudaEventRecord(E[1], c->stream));
+      record_event(c, E[1]);
       CKL(launch_spmm_f64(reinterpret_cast<SpmmDesc*>(dd + os) + is, reinterpret_cast<long long*>(dd + ops) + ips,
                           ns, sppre[ips + ns], c->stream));
-      CK(cudaEventRecord(E[2], c->stream));
+      record_event(c, E[2]);
       CKL(launch_gemm_f64(reinterpret_cast<GemmDesc*>(dd + o3) + i3, reinterpret_cast<long long*>(dd + op3) + ip3,
                           n3, g3pre[ip3 + n3], c->stream));
-      CK(cudaEventRecord(E[3], c->stream));
+      record_event(c, E[3]);
       c->launches += 3;
       i1 += n1;
       i3 += n3;
@@ -542,17 +632,14 @@ void run_contractions(tnqe_ctx* c, const std::vector<std::pair<int, int>>& pairs
     }
     CKL(launch_extract(reinterpret_cast<const double* const*>(dd + of), nw, d_H + p0, d_S + p0, c->stream));
     c->launches += 1;
-    CK(cudaStreamSynchronize(c->stream));   // the next wave reuses the workspace and the events
+    std::vector<std::array<int, 3>> reads;
     for (int t = 0; t < N; ++t) {
-      cudaEvent_t* E = &c->pev[2 + 6 * t];
-      float a = 0.f, b = 0.f, d = 0.f;
-      CK(cudaEventElapsedTime(&a, E[0], E[1]));
-      CK(cudaEventElapsedTime(&b, E[1], E[2]));
-      CK(cudaEventElapsedTime(&d, E[2], E[3]));
-      c->prof[1] += a;
-      c->prof[2] += b;
-      c->prof[3] += d;
+      const int e = 2 + 6 * t;
+      reads.push_back({e, e + 1, 1});
+      reads.push_back({e + 1, e + 2, 2});
+      reads.push_back({e + 2, e + 3, 3});
     }
+    site_events(c, fi, p1 == (size_t)np, reads);
     p0 = p1;
   }
 }
@@ -586,7 +673,7 @@ inline long long al64(long long x) { return (x + 63) & ~63LL; }   // floats -> 2
 inline int ld4(int x) { return (x + 3) & ~3; }
 
 void run_contractions_tc(tnqe_ctx* c, const std::vector<std::pair<int, int>>& pairs, const std::vector<KetView>& kets,
-                         double* d_H, double* d_S) {
+                         double* d_H, double* d_S, FinishInfo& fi) {
   const int N = c->N;
   const int np = (int)pairs.size();
   // per-pair FP32 workspace: two environments, X, Yt, packed ket / bra sites
@@ -741,9 +828,10 @@ void run_contractions_tc(tnqe_ctx* c, const std::vector<std::pair<int, int>>& pa
     const size_t bp1 = g1pre.size() * 8, bp3 = g3pre.size() * 8, bps = sppre.size() * 8, bpp = (packpre.size() + 1) * 8;
     const size_t bf = (size_t)nw * sizeof(float*);
     const size_t o1 = 0, o3 = o1 + al(b1), os = o3 + al(b3), opk = os + al(bs), op1 = opk + al(bpk),
-                 op3 = op1 + al(bp1), ops = op3 + al(bp3), opp = ops + al(bps), of = opp + al(bpp);
-    const size_t total = of + al(bf);
+                 op3 = op1 + al(bp1), ops = op3 + al(bp3), opp = ops + al(bps), of = opp + al(bpp), oe = of + al(bf);
+    const size_t total = oe + al(bf);
     std::vector<unsigned char> host(total, 0);
+    std::memcpy(host.data() + oe, env0.data(), bf);
     std::memcpy(host.data() + o1, g1.data(), b1);
     std::memcpy(host.data() + o3, g3.data(), b3);
     std::memcpy(host.data() + os, sp.data(), bs);
@@ -758,12 +846,9 @@ void run_contractions_tc(tnqe_ctx* c, const std::vector<std::pair<int, int>>& pa
     std::memcpy(host.data() + of, fin.data(), bf);
     c->tc_desc.ensure(total);
     unsigned char* dd = c->tc_desc.as<unsigned char>();
-    CK(cudaMemcpyAsync(dd, host.data(), total, cudaMemcpyHostToDevice, c->stream));
-    {
-      const float one = 1.0f;
-      for (int w = 0; w < nw; ++w)
-        CK(cudaMemcpyAsync(env0[w], &one, sizeof(float), cudaMemcpyHostToDevice, c->stream));
-    }
+    upload(c, dd, host.data(), total);
+    CKL(launch_unit_env_f32(reinterpret_cast<float* const*>(dd + oe), nw, c->stream));   // L_0 = 1
+    c->launches += 1;
     CKL(launch_pack_sites(reinterpret_cast<PackDesc*>(dd + opk), reinterpret_cast<long long*>(dd + opp),
                           (int)packs.size(), packtot, c->stream));
     c->launches += 1;
@@ -772,16 +857,16 @@ void run_contractions_tc(tnqe_ctx* c, const std::vector<std::pair<int, int>>& pa
     for (int t = 0; t < N; ++t) {
       const int n1 = g1n[t], n3 = g3n[t], ns = spn[t];
       cudaEvent_t* E = &c->pev[2 + 6 * t];
-      CK(cudaEventRecord(E[0], c->stream));
+      record_event(c, E[0]);
       CKL(launch_gemm_tf32x3(reinterpret_cast<TcGemmDesc*>(dd + o1) + i1, reinterpret_cast<long long*>(dd + op1) + ip1,
                              n1, g1pre[ip1 + n1], c->opt.max_spin, derr, c->stream));
-      CK(cudaEventRecord(E[1], c->stream));
+      record_event(c, E[1]);
       CKL(launch_spmm_t_f32(reinterpret_cast<SpmmTDesc*>(dd + os) + is, reinterpret_cast<long long*>(dd + ops) + ips,
                             ns, sppre[ips + ns], c->stream));
-      CK(cudaEventRecord(E[2], c->stream));
+      record_event(c, E[2]);
       CKL(launch_gemm_tf32x3(reinterpret_cast<TcGemmDesc*>(dd + o3) + i3, reinterpret_cast<long long*>(dd + op3) + ip3,
                              n3, g3pre[ip3 + n3], c->opt.max_spin, derr, c->stream));
-      CK(cudaEventRecord(E[3], c->stream));
+      record_event(c, E[3]);
       c->launches += 3;
       i1 += n1;
       i3 += n3;
@@ -792,22 +877,17 @@ void run_contractions_tc(tnqe_ctx* c, const std::vector<std::pair<int, int>>& pa
     }
     CKL(launch_extract_f32(reinterpret_cast<const float* const*>(dd + of), nw, 4, d_H + p0, d_S + p0, c->stream));
     c->launches += 1;
-    CK(cudaStreamSynchronize(c->stream));
+    std::vector<std::array<int, 3>> reads;
     for (int t = 0; t < N; ++t) {
-      cudaEvent_t* E = &c->pev[2 + 6 * t];
-      float a = 0.f, b = 0.f, d = 0.f;
-      CK(cudaEventElapsedTime(&a, E[0], E[1]));
-      CK(cudaEventElapsedTime(&b, E[1], E[2]));
-      CK(cudaEventElapsedTime(&d, E[2], E[3]));
-      c->prof[1] += a;
-      c->prof[2] += b;
-      c->prof[3] += d;
+      const int e = 2 + 6 * t;
+      reads.push_back({e, e + 1, 1});
+      reads.push_back({e + 1, e + 2, 2});
+      reads.push_back({e + 2, e + 3, 3});
     }
+    site_events(c, fi, p1 == (size_t)np, reads);
     p0 = p1;
   }
-  int herr = 0;
-  CK(cudaMemcpy(&herr, c->tc_err.p, sizeof(int), cudaMemcpyDeviceToHost));
-  if (herr) throw Error(TNQE_ERR_TIMEOUT, "a tensor-core pipeline wait ran out of iterations");
+  fi.check_err = true;
 }
 
 
@@ -816,11 +896,12 @@ inline long long ld8(long long x) { return (x + 7) & ~7LL; }
 inline size_t lz8(size_t x) { return (x + 7) & ~(size_t)7; }
 inline size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-// 3-D BF16 tensor map over slices [ns][rows][ldK] (K contiguous), box {32, 128, ns}, 64-byte swizzle
-void encode_slices(CUtensorMap* map, const __nv_bfloat16* base, long long rows, long long K, long long ldK, int ns) {
+// 3-D BF16 tensor map over slices [ns][rows][ldK] (K contiguous), box {32, box_rows, ns}, 64-byte swizzle
+void encode_slices(CUtensorMap* map, const __nv_bfloat16* base, long long rows, long long K, long long ldK, int ns,
+                   int box_rows) {
   cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)rows, (cuuint64_t)ns};
   cuuint64_t strides[2] = {(cuuint64_t)ldK * 2, (cuuint64_t)rows * ldK * 2};
-  cuuint32_t box[3] = {(cuuint32_t)OZ_BK, (cuuint32_t)OZ_BM, (cuuint32_t)ns};
+  cuuint32_t box[3] = {(cuuint32_t)OZ_BK, (cuuint32_t)box_rows, (cuuint32_t)ns};
   cuuint32_t es[3] = {1, 1, 1};
   const CUresult r = tensor_map_encoder()(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3,
                                           const_cast<__nv_bfloat16*>(base), dims, strides, box, es,
@@ -834,7 +915,7 @@ int slices_of(int precision) {
 }
 
 void run_contractions_oz(tnqe_ctx* c, const std::vector<std::pair<int, int>>& pairs, const std::vector<KetView>& kets,
-                         double* d_H, double* d_S) {
+                         double* d_H, double* d_S, FinishInfo& fi) {
   const int N = c->N;
   const int np = (int)pairs.size();
   const int ns = slices_of(c->opt.precision);
@@ -921,6 +1002,12 @@ void run_contractions_oz(tnqe_ctx* c, const std::vector<std::pair<int, int>>& pa
         }
       }
     }
+    int max_ncx = 4;
+    for (int w = 0; w < nw; ++w)
+      for (int t = 0; t < N; ++t) max_ncx = std::max(max_ncx, 4 * c->mps[pairs[p0 + w].first]->mpo.dims[t]);
+    int spmm_bw = spmm_df_smem_width(max_ncx);
+    if (c->tune.spmm_bw > 0 && spmm_bw > 0) spmm_bw = std::min(spmm_bw, c->tune.spmm_bw);
+    const int bn1 = c->tune.oz_bn1, bn3 = c->tune.oz_bn3;
     std::vector<SliceRowsDesc> sa;
     std::vector<SliceColsDesc> sb;
     std::vector<OzGemmDesc> g1, g3;
@@ -947,15 +1034,13 @@ void run_contractions_oz(tnqe_ctx* c, const std::vector<std::pair<int, int>>& pa
         d1.M = (int)MA;
         d1.N = 4 * cb2;
         d1.K = cb;
-        encode_slices(&d1.mapA, Asl[w], MA, cb, ld8(cb), ns);
-        encode_slices(&d1.mapB, ketS[w][t], 4LL * cb2, cb, ld8(cb), ns);
+        encode_slices(&d1.mapA, Asl[w], MA, cb, ld8(cb), ns, OZ_BM);
+        encode_slices(&d1.mapB, ketS[w][t], 4LL * cb2, cb, ld8(cb), ns, bn1);
         d1.ea = expA[w];
         d1.eb = ketE[w][t];
         d1.C = X[w];
         d1.ldc = d1.N;
-        d1.cg = d1.N;
-        d1.cld = 0;
-        d1.tiles_n = (d1.N + OZ_BN - 1) / OZ_BN;
+        d1.tiles_n = (d1.N + bn1 - 1) / bn1;
         d1.nslices = ns;
         g1pre.push_back(tiles1);
         tiles1 += (long long)((d1.M + OZ_BM - 1) / OZ_BM) * d1.tiles_n;
@@ -966,12 +1051,13 @@ void run_contractions_oz(tnqe_ctx* c, const std::vector<std::pair<int, int>>& pa
         s.ncols_x = 4 * Din;
         s.width = cb2;
         s.rowptr = bi.d_rowptr[t];
+        s.rowperm = bi.d_rowperm[t];
         s.col = bi.d_col[t];
         s.val = bi.d_valdf[t];
         s.X = X[w];
         s.Y = Y[w];
         sppre.push_back(tasks);
-        tasks += (long long)ca * 4 * Dout;
+        tasks += spmm_bw ? (long long)ca * ((cb2 + spmm_bw - 1) / spmm_bw) : (long long)ca * 4 * Dout;
         sp.push_back(s);
         // B slices: Y columns (w', b') over (a, k), K-major
         const long long NB = (long long)Dout * cb2;
@@ -985,15 +1071,13 @@ void run_contractions_oz(tnqe_ctx* c, const std::vector<std::pair<int, int>>& pa
         d3.M = ca2;
         d3.N = (int)NB;
         d3.K = 4 * ca;
-        encode_slices(&d3.mapA, braS[w][t], ca2, 4LL * ca, ld8(4 * ca), ns);
-        encode_slices(&d3.mapB, Bsl[w], NB, 4LL * ca, ld8(4 * ca), ns);
+        encode_slices(&d3.mapA, braS[w][t], ca2, 4LL * ca, ld8(4 * ca), ns, OZ_BM);
+        encode_slices(&d3.mapB, Bsl[w], NB, 4LL * ca, ld8(4 * ca), ns, bn3);
         d3.ea = braE[w][t];
         d3.eb = expB[w];
         d3.C = env[w];
         d3.ldc = NB;
-        d3.cg = d3.N;
-        d3.cld = 0;
-        d3.tiles_n = (d3.N + OZ_BN - 1) / OZ_BN;
+        d3.tiles_n = (d3.N + bn3 - 1) / bn3;
         d3.nslices = ns;
         g3pre.push_back(tiles3);
         tiles3 += (long long)((d3.M + OZ_BM - 1) / OZ_BM) * d3.tiles_n;
@@ -1044,52 +1128,182 @@ void run_contractions_oz(tnqe_ctx* c, const std::vector<std::pair<int, int>>& pa
     const size_t o_env = blob.put(env.data(), env.size() * sizeof(float2*));
     c->oz_desc.ensure(blob.h.size());
     unsigned char* dd = c->oz_desc.as<unsigned char>();
-    CK(cudaMemcpyAsync(dd, blob.h.data(), blob.h.size(), cudaMemcpyHostToDevice, c->stream));
-    CK(cudaEventRecord(c->pev[2 + 6 * N], c->stream));
+    upload(c, dd, blob.h.data(), blob.h.size());
+    record_event(c, c->pev[2 + 6 * N]);
     CKL(launch_unit_env(reinterpret_cast<float2* const*>(dd + o_env), nw, c->stream));
     CKL(launch_slice_sites(reinterpret_cast<SliceSiteDesc*>(dd + o_st), reinterpret_cast<long long*>(dd + o_stp),
                            (int)sites.size(), siterows, c->stream));
-    CK(cudaEventRecord(c->pev[3 + 6 * N], c->stream));
+    record_event(c, c->pev[3 + 6 * N]);
     c->launches += 2;
     size_t i = 0, ip = 0;
     for (int t = 0; t < N; ++t, i += nw, ip += nw + 1) {
       cudaEvent_t* E = &c->pev[2 + 6 * t];
       auto pre = [&](size_t off) { return reinterpret_cast<long long*>(dd + off) + ip; };
-      CK(cudaEventRecord(E[0], c->stream));
+      record_event(c, E[0]);
       CKL(launch_slice_rows(reinterpret_cast<SliceRowsDesc*>(dd + o_sa) + i, pre(o_sap), nw, sapre[ip + nw], c->stream));
-      CK(cudaEventRecord(E[1], c->stream));
+      record_event(c, E[1]);
       CKL(launch_gemm_bf16s(reinterpret_cast<OzGemmDesc*>(dd + o_g1) + i, pre(o_g1p), nw, g1pre[ip + nw],
-                            c->opt.max_spin, derr, c->stream));
-      CK(cudaEventRecord(E[2], c->stream));
-      CKL(launch_spmm_df(reinterpret_cast<SpmmDfDesc*>(dd + o_sp) + i, pre(o_spp), nw, sppre[ip + nw], c->stream));
-      CK(cudaEventRecord(E[3], c->stream));
+                            c->opt.max_spin, derr, bn1, c->stream));
+      record_event(c, E[2]);
+      if (spmm_bw)
+        CKL(launch_spmm_df_smem(reinterpret_cast<SpmmDfDesc*>(dd + o_sp) + i, pre(o_spp), nw, sppre[ip + nw], spmm_bw,
+                                max_ncx, c->stream));
+      else
+        CKL(launch_spmm_df(reinterpret_cast<SpmmDfDesc*>(dd + o_sp) + i, pre(o_spp), nw, sppre[ip + nw], c->stream));
+      record_event(c, E[3]);
       CKL(launch_slice_cols(reinterpret_cast<SliceColsDesc*>(dd + o_sb) + i, pre(o_sbp), nw, sbpre[ip + nw], c->stream));
-      CK(cudaEventRecord(E[4], c->stream));
+      record_event(c, E[4]);
       CKL(launch_gemm_bf16s(reinterpret_cast<OzGemmDesc*>(dd + o_g3) + i, pre(o_g3p), nw, g3pre[ip + nw],
-                            c->opt.max_spin, derr, c->stream));
-      CK(cudaEventRecord(E[5], c->stream));
+                            c->opt.max_spin, derr, bn3, c->stream));
+      record_event(c, E[5]);
       c->launches += 5;
     }
     CKL(launch_extract_df(reinterpret_cast<const float2* const*>(dd + o_env), nw, d_H + p0, d_S + p0, c->stream));
     c->launches += 1;
-    CK(cudaStreamSynchronize(c->stream));
-    float ms = 0.f;
-    CK(cudaEventElapsedTime(&ms, c->pev[2 + 6 * N], c->pev[3 + 6 * N]));
-    c->prof[10] += ms;
+    std::vector<std::array<int, 3>> reads{{2 + 6 * N, 3 + 6 * N, 10}};
     for (int t = 0; t < N; ++t) {
-      cudaEvent_t* E = &c->pev[2 + 6 * t];
-      float x[5];
-      for (int k = 0; k < 5; ++k) CK(cudaEventElapsedTime(&x[k], E[k], E[k + 1]));
-      c->prof[10] += x[0] + x[3];
-      c->prof[1] += x[1];
-      c->prof[2] += x[2];
-      c->prof[3] += x[4];
+      const int e = 2 + 6 * t;
+      reads.push_back({e, e + 1, 10});
+      reads.push_back({e + 1, e + 2, 1});
+      reads.push_back({e + 2, e + 3, 2});
+      reads.push_back({e + 3, e + 4, 10});
+      reads.push_back({e + 4, e + 5, 3});
     }
+    site_events(c, fi, p1 == (size_t)np, reads);
     p0 = p1;
   }
-  int herr = 0;
-  CK(cudaMemcpy(&herr, c->tc_err.p, sizeof(int), cudaMemcpyDeviceToHost));
-  if (herr) throw Error(TNQE_ERR_TIMEOUT, "a tensor-core pipeline wait ran out of iterations");
+  fi.check_err = true;
+}
+
+
+// ----------------------------------------------------------------------------- one matrix-element call
+// Everything the call puts on the stream, with no host synchronisation when the
+// contraction workspace fits one wave: rotations write capacity-padded states,
+// so the contraction is planned from the capacities alone.
+void enqueue_matrix_elements(tnqe_ctx* c, const std::vector<std::pair<int, int>>& pl, double* dH, double* dS,
+                             FinishInfo& fi) {
+  const int npairs = (int)pl.size();
+  c->launches = 0;
+  for (double& x : c->prof) x = 0.0;
+  record_event(c, c->ev[0]);
+  RotBatch rb;
+  run_rotations(c, pl, rb, 1);
+  record_event(c, c->ev[1]);
+  std::vector<KetView> kets(npairs);
+  for (int p = 0; p < npairs; ++p) {
+    const DevMps& mi = *c->mps[pl[p].first];
+    kets[p].base = mi.d_t;
+    kets[p].off = mi.off;
+    kets[p].dims = mi.dims;
+  }
+  for (size_t k = 0; k < rb.pair_idx.size(); ++k) {
+    KetView& kv = kets[rb.pair_idx[k]];
+    kv.base = rb.work[k];
+    kv.off = rb.woff[k];
+    kv.dims = rb.cap[k];
+  }
+  record_event(c, c->ev[2]);
+  if (c->opt.precision == TNQE_PREC_TF32X3) run_contractions_tc(c, pl, kets, dH, dS, fi);
+  else if (c->opt.precision >= TNQE_PREC_BF16X3) run_contractions_oz(c, pl, kets, dH, dS, fi);
+  else run_contractions(c, pl, kets, dH, dS, fi);
+  record_event(c, c->ev[3]);
+  fi.nrot = (int)rb.pair_idx.size();
+  if (fi.nrot) {
+    fi.rot_small = c->rot_small.as<unsigned char>();
+    fi.per_small = rb.per_small;
+    fi.o_stat = rb.o_stat;
+    fi.o_flops = rb.o_flops;
+    fi.ev_reads.push_back({0, 1, 0});
+  }
+  fi.pstat.assign(c->prof, c->prof + TNQE_PROFILE_LEN);
+  fi.launches = c->launches;
+}
+
+// After the stream has drained: rotation status and FLOPs, event timings, errors.
+void finish_matrix_elements(tnqe_ctx* c, const FinishInfo& fi) {
+  for (int k = 0; k < TNQE_PROFILE_LEN; ++k) c->prof[k] = fi.pstat.empty() ? 0.0 : fi.pstat[k];
+  c->launches = fi.launches;
+  int st = 0;
+  if (fi.nrot) {
+    std::vector<unsigned char> small(fi.per_small * fi.nrot);
+    CK(cudaMemcpy(small.data(), fi.rot_small, small.size(), cudaMemcpyDeviceToHost));
+    for (int k = 0; k < fi.nrot; ++k) {
+      int s1 = 0;
+      double f1 = 0.0;
+      std::memcpy(&s1, small.data() + fi.per_small * k + fi.o_stat, sizeof(int));
+      std::memcpy(&f1, small.data() + fi.per_small * k + fi.o_flops, sizeof(double));
+      st |= s1;
+      c->prof[4] += f1;
+    }
+  }
+  for (const auto& r : fi.ev_reads) {
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, c->pev[r[0]], c->pev[r[1]]));
+    c->prof[r[2]] += ms;
+  }
+  float t01 = 0, t23 = 0, t03 = 0;
+  CK(cudaEventElapsedTime(&t01, c->ev[0], c->ev[1]));
+  CK(cudaEventElapsedTime(&t23, c->ev[2], c->ev[3]));
+  CK(cudaEventElapsedTime(&t03, c->ev[0], c->ev[3]));
+  c->times[0] = t01;
+  c->times[1] = t23;
+  c->times[2] = t03;
+  if (fi.check_err) {
+    int herr = 0;
+    CK(cudaMemcpy(&herr, c->tc_err.p, sizeof(int), cudaMemcpyDeviceToHost));
+    if (herr) throw Error(TNQE_ERR_TIMEOUT, "a tensor-core pipeline wait ran out of iterations");
+  }
+  if (st & STATUS_OVERFLOW) throw Error(TNQE_ERR_STATE, "rotation scratch overflow");
+  if (st & STATUS_NOCONV)
+    throw Error(TNQE_ERR_NOCONV, "Jacobi SVD hit the sweep limit on a " + std::to_string((st >> 8) & 4095) + " x " +
+                                     std::to_string((st >> 20) & 4095) + " block (results written)");
+}
+
+std::vector<long long> graph_key(tnqe_ctx* c, const std::vector<std::pair<int, int>>& pl) {
+  long long cut = 0;
+  static_assert(sizeof(double) == sizeof(long long), "");
+  std::memcpy(&cut, &c->opt.cutoff, sizeof(cut));
+  std::vector<long long> k{c->generation, c->opt.precision, c->opt.chi_rot, cut, c->opt.renormalize_rotated,
+                           c->opt.max_jacobi_sweeps, c->opt.max_spin, c->tune.oz_bn1, c->tune.oz_bn3,
+                           c->tune.spmm_bw, (long long)pl.size()};
+  for (const auto& p : pl) k.push_back((long long)p.first * 65536 + p.second);
+  return k;
+}
+
+// Record the call into a CUDA graph for later replays.  The eager run that just
+// finished sized every workspace, so planning allocates nothing here; if it
+// would (or anything else fails), the capture is dropped and calls stay eager.
+void capture_matrix_elements(tnqe_ctx* c, const std::vector<std::pair<int, int>>& pl, const std::vector<long long>& key,
+                             double* dH, double* dS) {
+  double prof_keep[TNQE_PROFILE_LEN];
+  std::copy(c->prof, c->prof + TNQE_PROFILE_LEN, prof_keep);
+  const int launches_keep = c->launches;
+  auto ge = std::make_unique<GraphEntry>();
+  const unsigned long long epoch0 = g_alloc_epoch.load();
+  bool ok = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeRelaxed) == cudaSuccess;
+  if (ok) {
+    c->capturing = true;
+    c->cap_uploads = &ge->uploads;
+    try {
+      enqueue_matrix_elements(c, pl, dH, dS, ge->fin);
+    } catch (const Error&) {
+      ok = false;
+    }
+    c->capturing = false;
+    c->cap_uploads = nullptr;
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+    ok = ok && e == cudaSuccess && g != nullptr && g_alloc_epoch.load() == epoch0;
+    if (ok) ok = cudaGraphInstantiate(&ge->exec, g, 0) == cudaSuccess;
+    if (g) cudaGraphDestroy(g);
+  }
+  cudaGetLastError();   // a failed capture leaves no sticky error behind
+  std::copy(prof_keep, prof_keep + TNQE_PROFILE_LEN, c->prof);
+  c->launches = launches_keep;
+  if (!ok) return;
+  ge->epoch = epoch0;
+  if (c->graphs.size() >= 16) c->graphs.erase(c->graphs.begin());
+  c->graphs[key] = std::move(ge);
 }
 
 void check_ctx(tnqe_ctx* c) {
@@ -1209,6 +1423,13 @@ void prepare_mps(tnqe_ctx* c, const double* const* tensors, const int* bond_dims
     m.d_rowptr.push_back(dalloc_copy(m.mpo.sites[t].rowptr, m.owned));
     m.d_col.push_back(dalloc_copy(m.mpo.sites[t].col, m.owned));
     m.d_val.push_back(dalloc_copy(m.mpo.sites[t].val, m.owned));
+    {
+      const std::vector<int>& rp = m.mpo.sites[t].rowptr;
+      std::vector<int> perm(rp.size() - 1);
+      for (size_t r = 0; r < perm.size(); ++r) perm[r] = (int)r;
+      std::stable_sort(perm.begin(), perm.end(), [&](int x, int y) { return rp[x + 1] - rp[x] > rp[y + 1] - rp[y]; });
+      m.d_rowperm.push_back(dalloc_copy(perm, m.owned));
+    }
     std::vector<float> v32(m.mpo.sites[t].val.begin(), m.mpo.sites[t].val.end());
     m.d_val32.push_back(dalloc_copy(v32, m.owned));
     std::vector<float2> vdf(v32.size());
@@ -1237,6 +1458,7 @@ void tnqe_default_options(tnqe_options* o) {
   o->max_spin = 1LL << 26;
   o->cuda_stream = nullptr;
   o->device = 0;
+  o->use_graphs = 1;
 }
 
 tnqe_status tnqe_create(const double* h1, const double* eri, int N, int n_alpha, int n_beta,
@@ -1300,6 +1522,8 @@ tnqe_status tnqe_add_mps(tnqe_ctx* c, const double* const* tensors, const int* b
       throw;
     }
     c->mps.push_back(std::move(m));
+    ++c->generation;
+    clear_graphs(c);
     if (mps_id) *mps_id = (int)c->mps.size() - 1;
     return TNQE_OK;
   } catch (const Error& e) {
@@ -1313,6 +1537,8 @@ tnqe_status tnqe_reset_mps(tnqe_ctx* c) {
   try {
     check_ctx(c);
     CK(cudaStreamSynchronize(c->stream));
+    clear_graphs(c);
+    ++c->generation;
     for (auto& m : c->mps) m->free_all();
     c->mps.clear();
     for (auto& kv : c->plans)
@@ -1340,7 +1566,7 @@ tnqe_status tnqe_rotate(tnqe_ctx* c, int i, int j, double* discarded_weight) {
       return TNQE_OK;
     }
     RotBatch rb;
-    run_rotations(c, {{i, j}}, rb);
+    run_rotations(c, {{i, j}}, rb, 0);
     std::vector<std::vector<int>> dims;
     std::vector<double> disc;
     int st = 0;
@@ -1395,57 +1621,37 @@ tnqe_status tnqe_matrix_elements(tnqe_ctx* c, const int* pairs, int npairs, doub
       if (i > j) throw Error(TNQE_ERR_ARG, "pairs must have i <= j");
       pl[p] = {i, j};
     }
-    c->launches = 0;
     c->kept_pair_valid = 0;
-    for (double& x : c->prof) x = 0.0;
-    const int N = c->N;
-    CK(cudaEventRecord(c->ev[0], c->stream));
-    RotBatch rb;
-    run_rotations(c, pl, rb);
-    CK(cudaEventRecord(c->ev[1], c->stream));
-    std::vector<std::vector<int>> rdims;
-    std::vector<double> disc;
-    int st = 0;
-    fetch_rotation_results(c, rb, rdims, disc, st);
-    if (st & STATUS_OVERFLOW) throw Error(TNQE_ERR_STATE, "rotation scratch overflow");
-    std::vector<KetView> kets(npairs);
-    for (int p = 0; p < npairs; ++p) {
-      const DevMps& mi = *c->mps[pl[p].first];
-      kets[p].base = mi.d_t;
-      kets[p].off = mi.off;
-      kets[p].dims = mi.dims;
-    }
-    for (size_t k = 0; k < rb.pair_idx.size(); ++k) {
-      KetView& kv = kets[rb.pair_idx[k]];
-      kv.base = rb.work[k];
-      kv.off = rb.woff[k];
-      kv.dims = rdims[k];
-    }
-    CK(cudaEventRecord(c->ev[2], c->stream));
     c->con_out.ensure(sizeof(double) * 2 * npairs);
     double* dH = c->con_out.as<double>();
     double* dS = dH + npairs;
-    if (c->opt.precision == TNQE_PREC_TF32X3) run_contractions_tc(c, pl, kets, dH, dS);
-    else if (c->opt.precision >= TNQE_PREC_BF16X3) run_contractions_oz(c, pl, kets, dH, dS);
-    else run_contractions(c, pl, kets, dH, dS);
-    CK(cudaEventRecord(c->ev[3], c->stream));
+    GraphEntry* ge = nullptr;
+    std::vector<long long> key;
+    if (c->opt.use_graphs) {
+      key = graph_key(c, pl);
+      auto it = c->graphs.find(key);
+      if (it != c->graphs.end() && it->second->epoch == g_alloc_epoch.load()) ge = it->second.get();
+    }
+    FinishInfo fi;
+    if (ge) {
+      for (const Upload& u : ge->uploads)
+        CK(cudaMemcpyAsync(u.dst, u.data.data(), u.data.size(), cudaMemcpyHostToDevice, c->stream));
+      CK(cudaGraphLaunch(ge->exec, c->stream));
+      fi = ge->fin;
+    } else {
+      enqueue_matrix_elements(c, pl, dH, dS, fi);
+    }
     const bool hdev = is_device_ptr(H_out), sdev = is_device_ptr(S_out);
     CK(cudaMemcpyAsync(H_out, dH, sizeof(double) * npairs, hdev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                        c->stream));
     CK(cudaMemcpyAsync(S_out, dS, sizeof(double) * npairs, sdev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                        c->stream));
     CK(cudaStreamSynchronize(c->stream));
-    float t01 = 0, t23 = 0, t03 = 0;
-    CK(cudaEventElapsedTime(&t01, c->ev[0], c->ev[1]));
-    CK(cudaEventElapsedTime(&t23, c->ev[2], c->ev[3]));
-    CK(cudaEventElapsedTime(&t03, c->ev[0], c->ev[3]));
-    c->times[0] = t01;
-    c->times[1] = t23;
-    c->times[2] = t03;
-    (void)N;
-    if (st & STATUS_NOCONV)
-      throw Error(TNQE_ERR_NOCONV, "Jacobi SVD hit the sweep limit on a " + std::to_string((st >> 8) & 4095) + " x " +
-                                       std::to_string((st >> 20) & 4095) + " block (results written)");
+    finish_matrix_elements(c, fi);
+    if (c->opt.use_graphs && !ge && fi.single_wave) {
+      if (c->seen.size() > 64) c->seen.clear();
+      if (c->seen[key]++ >= 1) capture_matrix_elements(c, pl, key, dH, dS);
+    }
     return TNQE_OK;
   } catch (const Error& e) {
     return fail(c, e);
@@ -1453,6 +1659,83 @@ tnqe_status tnqe_matrix_elements(tnqe_ctx* c, const int* pairs, int npairs, doub
     return fail(c, Error(TNQE_ERR_NOMEM, e.what()));
   }
 }
+
+tnqe_status tnqe_autotune(tnqe_ctx* c, const int* pairs, int npairs, int* config, double* times) {
+  try {
+    check_ctx(c);
+    if (npairs <= 0 || !pairs) throw Error(TNQE_ERR_ARG, "bad pair list");
+    if (c->opt.precision >= TNQE_PREC_BF16X3) {
+      struct Cand {
+        int bn1, bn3, bw;
+      };
+      const Cand cands[3] = {{128, 128, 8}, {64, 64, 4}, {128, 128, 2}};
+      const int keep_graphs = c->opt.use_graphs;
+      c->opt.use_graphs = 0;
+      std::vector<double> Hh(npairs), Sh(npairs);
+      double t[3][3];
+      tnqe_status st = TNQE_OK;
+      for (int k = 0; k < 3 && st == TNQE_OK; ++k) {
+        c->tune.oz_bn1 = cands[k].bn1;
+        c->tune.oz_bn3 = cands[k].bn3;
+        c->tune.spmm_bw = cands[k].bw;
+        for (int rep = 0; rep < 2 && st == TNQE_OK; ++rep)   // the first run warms allocations and caches
+          st = tnqe_matrix_elements(c, pairs, npairs, Hh.data(), Sh.data());
+        t[k][0] = c->prof[1];
+        t[k][1] = c->prof[3];
+        t[k][2] = c->prof[2];
+        if (times)
+          for (int q = 0; q < 3; ++q) times[3 * k + q] = t[k][q];
+      }
+      c->opt.use_graphs = keep_graphs;
+      if (st != TNQE_OK) return st;
+      int b1 = 0, b3 = 0, bw = 0;
+      for (int k = 1; k < 3; ++k) {
+        if (t[k][0] < t[b1][0]) b1 = k;
+        if (t[k][1] < t[b3][1]) b3 = k;
+        if (t[k][2] < t[bw][2]) bw = k;
+      }
+      c->tune.oz_bn1 = cands[b1].bn1;
+      c->tune.oz_bn3 = cands[b3].bn3;
+      c->tune.spmm_bw = cands[bw].bw;
+      CK(cudaStreamSynchronize(c->stream));
+      clear_graphs(c);
+    }
+    if (config) {
+      config[0] = c->tune.oz_bn1;
+      config[1] = c->tune.oz_bn3;
+      config[2] = c->tune.spmm_bw;
+    }
+    return TNQE_OK;
+  } catch (const Error& e) {
+    return fail(c, e);
+  }
+}
+
+tnqe_status tnqe_set_tuning(tnqe_ctx* c, int bn1, int bn3, int spmm_bw) {
+  if (!c) return TNQE_ERR_ARG;
+  if ((bn1 != 64 && bn1 != 128) || (bn3 != 64 && bn3 != 128) || spmm_bw < 0 || spmm_bw > 8 ||
+      (spmm_bw & (spmm_bw - 1))) {
+    c->err = "tile choices: bn1, bn3 in {64, 128}; spmm_bw in {0, 1, 2, 4, 8}";
+    return TNQE_ERR_ARG;
+  }
+  c->tune.oz_bn1 = bn1;
+  c->tune.oz_bn3 = bn3;
+  c->tune.spmm_bw = spmm_bw;
+  return TNQE_OK;
+}
+
+tnqe_status tnqe_clear_graphs(tnqe_ctx* c) {
+  try {
+    check_ctx(c);
+    CK(cudaStreamSynchronize(c->stream));
+    clear_graphs(c);
+    return TNQE_OK;
+  } catch (const Error& e) {
+    return fail(c, e);
+  }
+}
+
+int tnqe_graph_count(const tnqe_ctx* c) { return c ? (int)c->graphs.size() : 0; }
 
 tnqe_status tnqe_solve(tnqe_ctx* c, const double* H, const double* S, int M, double* E, double* C, int* rank_kept,
                        double* kappa1) {
@@ -1532,6 +1815,9 @@ void tnqe_destroy(tnqe_ctx* c) {
   c->tc_ws.release();
   c->tc_desc.release();
   c->tc_err.release();
+  c->oz_ws.release();
+  c->oz_desc.release();
+  c->graphs.clear();
   for (auto& e : c->ev)
     if (e) cudaEventDestroy(e);
   for (auto& e : c->pev)

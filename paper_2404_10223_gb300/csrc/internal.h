@@ -60,6 +60,7 @@ Mpo build_mpo(const double* h1, const double* eri, int N);
 // ----------------------------------------------------------------------------- device descriptors
 struct RotDesc {
   int N, chi_rot, ngates, neg_site, renorm, max_sweeps;
+  int pad_out, pad_;              // pad_out: leave every site as [cap_l][4][cap_r], zero-filled
   double cutoff;
   const double* src;              // input MPS j
   const long long* src_off;       // N site offsets into src
@@ -145,6 +146,7 @@ struct SliceSiteDesc {            // FP64 site tensor [cl][4][cr] -> K-major sli
 struct SpmmDfDesc {               // Y[a][row][:] = sum val * X[a][col][:] in double-float
   int chi_a, nrows, ncols_x, width;
   const int* rowptr;
+  const int* rowperm;             // rows by descending nonzero count
   const int* col;
   const float2* val;
   const float2* X;
@@ -172,10 +174,16 @@ int launch_slice_rows(const SliceRowsDesc* d, const long long* prefix, int n, lo
 int launch_slice_cols(const SliceColsDesc* d, const long long* prefix, int n, long long blocks, void* stream);
 int launch_slice_sites(const SliceSiteDesc* d, const long long* prefix, int n, long long rows, void* stream);
 int launch_spmm_df(const SpmmDfDesc* d, const long long* prefix, int n, long long total, void* stream);
+// shared-memory form: one CTA per (problem, a, bw ket columns); prefix counts CTAs
+int spmm_df_smem_width(int max_ncols_x);   // bw in {8, 4, 2, 1}, 0 if the X slab does not fit
+int launch_spmm_df_smem(const SpmmDfDesc* d, const long long* prefix, int n, long long blocks, int bw,
+                        int max_ncols_x, void* stream);
 int launch_unit_env(float2* const* env, int n, void* stream);
+int launch_unit_env_f64(double* const* env, int n, void* stream);
+int launch_unit_env_f32(float* const* env, int n, void* stream);
 int launch_extract_df(const float2* const* fin, int npairs, double* H, double* S, void* stream);
 int launch_gemm_bf16s(const OzGemmDesc* d, const long long* tile_prefix, int nprob, long long total_tiles,
-                      long long max_spin, int* err, void* stream);
+                      long long max_spin, int* err, int bn, void* stream);
 int launch_solve(const double* d_H, const double* d_S, int M, double eps, int max_sweeps,
                  double* d_E, double* d_C, int* d_rank, double* d_kappa, int* d_status, void* stream);
 

@@ -211,9 +211,67 @@ __global__ void __launch_bounds__(256) spmm_df_kernel(const SpmmDfDesc* __restri
   }
 }
 
+// Y[a][row][b0:b0+BW] for every row, with X[a][:][b0:b0+BW] staged in shared
+// memory once (each X element is read by every nonzero of its column).
+// Threads take (row, column) pairs; rows go in descending nonzero count so the
+// BW-lane groups of a warp carry similar loop lengths.
+constexpr int SPMM_SMEM_BYTES = 112 * 1024;
+template <int BW>
+__global__ void __launch_bounds__(256, 2) spmm_df_smem_kernel(const SpmmDfDesc* __restrict__ descs,
+                                                           const long long* __restrict__ prefix, int nprob) {
+  extern __shared__ float2 xs[];
+  const long long task = blockIdx.x;
+  const int p = find_prob(prefix, nprob, task);
+  const SpmmDfDesc& d = descs[p];
+  const int nbt = (d.width + BW - 1) / BW;
+  const long long local = task - prefix[p];
+  const int a = (int)(local / nbt), b0 = (int)(local % nbt) * BW;
+  const int tid = threadIdx.x;
+  const float2* Xa = d.X + (long long)a * d.ncols_x * d.width + b0;
+  for (int i = tid; i < d.ncols_x * BW; i += 256) {
+    const int r = i / BW, c = i % BW;
+    xs[i] = (b0 + c < d.width) ? Xa[(long long)r * d.width + c] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  // each thread: one row, columns c and c + BW/2 (two independent accumulations)
+  constexpr int HW = BW > 1 ? BW / 2 : 1;
+  constexpr int NC = BW > 1 ? 2 : 1;
+  const int c = tid % HW;
+  float2* Ya = d.Y + (long long)a * d.nrows * d.width + b0;
+  for (int r0 = 0; r0 < d.nrows; r0 += 256 / HW) {
+    const int rr = r0 + tid / HW;
+    if (rr >= d.nrows) break;
+    const int row = d.rowperm[rr];
+    const int e0 = d.rowptr[row], e1 = d.rowptr[row + 1];
+    float ah[NC], al[NC];
+#pragma unroll
+    for (int u = 0; u < NC; ++u) ah[u] = al[u] = 0.f;
+    for (int e = e0; e < e1; ++e) {
+      const float2 v = d.val[e];
+      const float2* xr = xs + d.col[e] * BW + c;
+#pragma unroll
+      for (int u = 0; u < NC; ++u) {
+        const float2 x = xr[u * HW];
+        df_fma(v.x, v.y, x.x, x.y, ah[u], al[u]);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < NC; ++u)
+      if (b0 + c + u * HW < d.width) Ya[(long long)row * d.width + c + u * HW] = df_norm(ah[u], al[u]);
+  }
+}
+
 __global__ void unit_env_kernel(float2* const* __restrict__ env, int n) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p < n) env[p][0] = make_float2(1.f, 0.f);
+}
+__global__ void unit_env_f64_kernel(double* const* __restrict__ env, int n) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < n) env[p][0] = 1.0;
+}
+__global__ void unit_env_f32_kernel(float* const* __restrict__ env, int n) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < n) env[p][0] = 1.f;
 }
 
 __global__ void extract_df_kernel(const float2* const* __restrict__ fin, int npairs, double* H, double* S) {
@@ -246,9 +304,54 @@ int launch_spmm_df(const SpmmDfDesc* d, const long long* prefix, int n, long lon
   spmm_df_kernel<<<(unsigned)((total + 7) / 8), 256, 0, (cudaStream_t)stream>>>(d, prefix, n, total);
   return (int)cudaGetLastError();
 }
+int spmm_df_smem_width(int max_ncols_x) {
+  for (int bw = 8; bw >= 1; bw >>= 1)
+    if ((long long)max_ncols_x * bw * (long long)sizeof(float2) <= SPMM_SMEM_BYTES) return bw;
+  return 0;
+}
+int launch_spmm_df_smem(const SpmmDfDesc* d, const long long* prefix, int n, long long blocks, int bw,
+                        int max_ncols_x, void* stream) {
+  if (blocks <= 0) return 0;
+  const size_t smem = (size_t)max_ncols_x * bw * sizeof(float2);
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaSuccess;
+  switch (bw) {
+    case 8:
+      e = cudaFuncSetAttribute(spmm_df_smem_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, SPMM_SMEM_BYTES);
+      if (e == cudaSuccess) spmm_df_smem_kernel<8><<<(unsigned)blocks, 256, smem, st>>>(d, prefix, n);
+      break;
+    case 4:
+      e = cudaFuncSetAttribute(spmm_df_smem_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, SPMM_SMEM_BYTES);
+      if (e == cudaSuccess) spmm_df_smem_kernel<4><<<(unsigned)blocks, 256, smem, st>>>(d, prefix, n);
+      break;
+    case 2:
+      e = cudaFuncSetAttribute(spmm_df_smem_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, SPMM_SMEM_BYTES);
+      if (e == cudaSuccess) spmm_df_smem_kernel<2><<<(unsigned)blocks, 256, smem, st>>>(d, prefix, n);
+      break;
+    case 1:
+      e = cudaFuncSetAttribute(spmm_df_smem_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, SPMM_SMEM_BYTES);
+      if (e == cudaSuccess) spmm_df_smem_kernel<1><<<(unsigned)blocks, 256, smem, st>>>(d, prefix, n);
+      break;
+    default:
+      return (int)cudaErrorInvalidValue;
+  }
+  if (e != cudaSuccess) return (int)e;
+  return (int)cudaGetLastError();
+}
+
 int launch_unit_env(float2* const* env, int n, void* stream) {
   if (n <= 0) return 0;
   unit_env_kernel<<<(n + 127) / 128, 128, 0, (cudaStream_t)stream>>>(env, n);
+  return (int)cudaGetLastError();
+}
+int launch_unit_env_f64(double* const* env, int n, void* stream) {
+  if (n <= 0) return 0;
+  unit_env_f64_kernel<<<(n + 127) / 128, 128, 0, (cudaStream_t)stream>>>(env, n);
+  return (int)cudaGetLastError();
+}
+int launch_unit_env_f32(float* const* env, int n, void* stream) {
+  if (n <= 0) return 0;
+  unit_env_f32_kernel<<<(n + 127) / 128, 128, 0, (cudaStream_t)stream>>>(env, n);
   return (int)cudaGetLastError();
 }
 int launch_extract_df(const float2* const* fin, int npairs, double* H, double* S, void* stream) {
@@ -257,13 +360,22 @@ int launch_extract_df(const float2* const* fin, int npairs, double* H, double* S
   return (int)cudaGetLastError();
 }
 int launch_gemm_bf16s(const OzGemmDesc* d, const long long* tile_prefix, int nprob, long long total_tiles,
-                      long long max_spin, int* err, void* stream) {
+                      long long max_spin, int* err, int bn, void* stream) {
   if (total_tiles <= 0) return 0;
-  const cudaError_t e =
-      cudaFuncSetAttribute(gemm_bf16s_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM_BYTES);
-  if (e != cudaSuccess) return (int)e;
-  gemm_bf16s_kernel<<<(unsigned)total_tiles, OZ_THREADS, OZ_SMEM_BYTES, (cudaStream_t)stream>>>(d, tile_prefix, nprob,
-                                                                                               max_spin, err);
+  cudaStream_t st = (cudaStream_t)stream;
+  if (bn == 128) {
+    const cudaError_t e =
+        cudaFuncSetAttribute(gemm_bf16s_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM_BYTES);
+    if (e != cudaSuccess) return (int)e;
+    gemm_bf16s_kernel<128><<<(unsigned)total_tiles, OZ_THREADS, OZ_SMEM_BYTES, st>>>(d, tile_prefix, nprob, max_spin, err);
+  } else if (bn == 64) {
+    const cudaError_t e =
+        cudaFuncSetAttribute(gemm_bf16s_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM_BYTES);
+    if (e != cudaSuccess) return (int)e;
+    gemm_bf16s_kernel<64><<<(unsigned)total_tiles, OZ_THREADS, OZ_SMEM_BYTES, st>>>(d, tile_prefix, nprob, max_spin, err);
+  } else {
+    return (int)cudaErrorInvalidValue;
+  }
   return (int)cudaGetLastError();
 }
 

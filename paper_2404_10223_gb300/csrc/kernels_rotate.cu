@@ -786,6 +786,29 @@ __global__ void __launch_bounds__(RT_THREADS) rotate_pairs_kernel(const RotDesc*
     const double f = t1 > 0.0 ? sqrt(t0 / t1) : 1.0;
     for (long long x = tid; x < n; x += RT_THREADS) T[x] *= f;
   }
+  // ---- optional capacity layout: site s becomes [cap_s][4][cap_{s+1}] with zeros
+  // beyond the kept dimensions (staged through the theta scratch, which the host
+  // sizes to hold any one site at capacity)
+  if (D.pad_out) {
+    __syncthreads();
+    for (int s = 0; s < N; ++s) {
+      const int cl = D.work_dims[s], cr = D.work_dims[s + 1];
+      const int Cl = D.work_cap[s], Cr = D.work_cap[s + 1];
+      if (cl == Cl && cr == Cr) continue;
+      double* T = D.work + D.work_off[s];
+      const long long n = (long long)cl * 4 * cr;
+      for (long long x = tid; x < n; x += RT_THREADS) D.theta[x] = T[x];
+      __syncthreads();
+      const long long np = (long long)Cl * 4 * Cr;
+      for (long long x = tid; x < np; x += RT_THREADS) {
+        const int r = (int)(x % Cr);
+        const long long lk = x / Cr;
+        const int l = (int)(lk / 4), k = (int)(lk % 4);
+        T[x] = (l < cl && r < cr) ? D.theta[((long long)l * 4 + k) * cr + r] : 0.0;
+      }
+      __syncthreads();
+    }
+  }
   if (tid == 0) {
     *D.discarded = s_disc;
     *D.status = s_status;

@@ -15,10 +15,11 @@
 // accumulators error-free into a double-float (hi + lo, two FP32 values) and
 // scales by 2^(e_r + e_c).
 //
-// One CTA computes one 128 x 128 tile of one problem: thread 0 issues the TMA
-// loads (3-D boxes: 32 K-elements x 128 rows x S slices, 64-byte swizzle) and
-// the tcgen05.mma instructions; the four accumulators fill the 512 columns of
-// tensor memory; all four warps run the epilogue.
+// One CTA computes one 128 x BN tile (BN = 128 or 64) of one problem: thread 0
+// issues the TMA loads (3-D boxes: 32 K-elements x rows x S slices, 64-byte
+// swizzle) and the tcgen05.mma instructions; the four accumulators take 4 BN
+// columns of tensor memory; all four warps run the epilogue, staged through
+// shared memory for row-contiguous stores.
 #pragma once
 #include <cuda.h>
 #include <cuda_runtime.h>
@@ -26,7 +27,8 @@
 
 namespace tnqe {
 
-constexpr int OZ_BM = 128, OZ_BN = 128, OZ_BK = 32;    // BK in BF16 elements (64 bytes)
+constexpr int OZ_BM = 128, OZ_BK = 32;                 // BK in BF16 elements (64 bytes)
+constexpr int OZ_BN_MAX = 128;                         // N tile: 128 or 64 (chosen per GEMM by the tuner)
 constexpr int OZ_MAXS = 5;                             // slices per operand
 constexpr int OZ_MAXK = 1024;                          // exactness bound of acc0..acc2
 constexpr int OZ_THREADS = 128;
@@ -35,25 +37,25 @@ constexpr int OZ_MAX_STAGES = 4;
 constexpr int OZ_STAGE_AREA = 196608;                  // pipeline stages: 2 S slice tiles each
 constexpr int OZ_GUARD = 16384;                        // slack after the stage area
 constexpr int OZ_SMEM_BYTES = OZ_STAGE_AREA + OZ_GUARD + 1024 /*align*/ + 256 /*barriers*/;
-constexpr int OZ_TMEM_COLS = 512;
-// pipeline depth for S slices: as many stages of 2 S tiles as fit the stage area
-__host__ __device__ constexpr int oz_stages(int S) {
-  return (OZ_STAGE_AREA / (2 * S * OZ_SLICE_BYTES)) < OZ_MAX_STAGES ? (OZ_STAGE_AREA / (2 * S * OZ_SLICE_BYTES))
-                                                                    : OZ_MAX_STAGES;
+// bytes of one pipeline stage: S slice tiles of A (128 rows) and of B (BN rows)
+__host__ __device__ constexpr int oz_stage_bytes(int S, int BN) { return S * (OZ_SLICE_BYTES + BN * OZ_BK * 2); }
+// pipeline depth: as many stages as fit the stage area
+__host__ __device__ constexpr int oz_stages(int S, int BN) {
+  return (OZ_STAGE_AREA / oz_stage_bytes(S, BN)) < OZ_MAX_STAGES ? (OZ_STAGE_AREA / oz_stage_bytes(S, BN))
+                                                                 : OZ_MAX_STAGES;
 }
 
 struct OzGemmDesc {     // CUtensorMap members carry the required alignment
   CUtensorMap mapA;     // dims {K, M, S}: slice s of row m at A + (s * M + m) * ldK, box {32, 128, S}
-  CUtensorMap mapB;     // dims {K, N, S}
+  CUtensorMap mapB;     // dims {K, N, S}, box {32, BN, S}
   const int* ea;        // M row exponents of A
   const int* eb;        // N row exponents of B
-  float2* C;            // element (m, n) at C + m * ldc + (n / cg) * cld + n % cg, as (hi, lo)
+  float2* C;            // element (m, n) at C + m * ldc + n, as (hi, lo)
   long long ldc;
   int M, N, K;
-  int cg, cld;
   int tiles_n;
   int nslices;          // 2 .. 5
-  int pad;
+  int pad[3];
 };
 
 #if defined(__CUDACC__) && defined(TNQE_DEFINE_OZ_KERNEL)
@@ -139,9 +141,11 @@ __device__ __forceinline__ uint64_t sw64_desc(uint32_t saddr) {
   d |= (uint64_t)4 << 61;            // SWIZZLE_64B
   return d;
 }
-// kind::f16 with BF16 A and B, FP32 accumulator, both K-major, M = 128, N = 128
-constexpr uint32_t OZ_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(OZ_BN >> 3) << 17) |
-                              ((uint32_t)(OZ_BM >> 4) << 24);
+// kind::f16 with BF16 A and B, FP32 accumulator, both K-major, M = 128, N = BN
+template <int BN>
+__host__ __device__ constexpr uint32_t oz_idesc() {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(OZ_BM >> 4) << 24);
+}
 
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   s = a + b;
@@ -158,6 +162,7 @@ __device__ __forceinline__ float pow2f(int e) {
 
 constexpr int OZ_ERR_TIMEOUT = 1;
 
+template <int BN>
 __global__ void __launch_bounds__(OZ_THREADS, 1)
     gemm_bf16s_kernel(const OzGemmDesc* __restrict__ descs, const long long* __restrict__ tile_prefix, int nprob,
                       long long max_spin, int* __restrict__ err) {
@@ -169,6 +174,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
   uint64_t* accb = empty + OZ_MAX_STAGES;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accb + 1);
   __shared__ int s_fail;
+  __shared__ int s_eb[BN];
+  constexpr int TMEM_COLS = 4 * BN;                      // four accumulators
+  constexpr uint32_t IDESC = oz_idesc<BN>();
 
   const long long tile = blockIdx.x;
   int lo = 0, hi = nprob - 1;
@@ -179,12 +187,12 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
   const OzGemmDesc* d = descs + lo;
   const long long local = tile - tile_prefix[lo];
   const int tm = (int)(local / d->tiles_n), tn = (int)(local % d->tiles_n);
-  const int m0 = tm * OZ_BM, n0 = tn * OZ_BN;
+  const int m0 = tm * OZ_BM, n0 = tn * BN;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int KT = (d->K + OZ_BK - 1) / OZ_BK;
   const int S = d->nslices;
-  const int NST = oz_stages(S);
-  const int stage_bytes = 2 * S * OZ_SLICE_BYTES;
+  const int NST = oz_stages(S, BN);
+  const int stage_bytes = oz_stage_bytes(S, BN);
 
   if (tid == 0) {
     s_fail = 0;
@@ -196,7 +204,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     fence_mbar_init();
   }
   if (warp == 0) {
-    tmem_alloc(tmem_slot, OZ_TMEM_COLS);
+    tmem_alloc(tmem_slot, TMEM_COLS);
     tmem_relinquish();
   }
   tc_fence_before();
@@ -206,7 +214,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
 
   int fail = 0;
   if (tid == 0) {
-    const uint32_t tx = (uint32_t)(2 * S * OZ_SLICE_BYTES);
+    const uint32_t tx = (uint32_t)stage_bytes;
     auto stage_a = [&](int s) { return smem + s * stage_bytes; };
     auto stage_b = [&](int s) { return smem + s * stage_bytes + S * OZ_SLICE_BYTES; };
     auto issue = [&](int s, int kt) {
@@ -230,16 +238,16 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       for (int k = 0; k < OZ_BK / 16; ++k) {        // 16 BF16 = 32 bytes per MMA along K
         const uint32_t acc_on = (kt > 0 || k > 0) ? 1u : 0u;
         auto da = [&](int i) { return sw64_desc(a0 + i * OZ_SLICE_BYTES + 32 * k); };
-        auto db = [&](int j) { return sw64_desc(b0 + j * OZ_SLICE_BYTES + 32 * k); };
-        mma_bf16(tmem + 0 * OZ_BN, da(0), db(0), OZ_IDESC, acc_on);
-        mma_bf16(tmem + 1 * OZ_BN, da(0), db(1), OZ_IDESC, acc_on);
-        mma_bf16(tmem + 2 * OZ_BN, da(1), db(0), OZ_IDESC, acc_on);
+        auto db = [&](int j) { return sw64_desc(b0 + j * (BN * OZ_BK * 2) + 32 * k); };
+        mma_bf16(tmem + 0 * BN, da(0), db(0), IDESC, acc_on);
+        mma_bf16(tmem + 1 * BN, da(0), db(1), IDESC, acc_on);
+        mma_bf16(tmem + 2 * BN, da(1), db(0), IDESC, acc_on);
         // orders 4 .. S + 1 into acc3 (0-based slice indices i + j = 2 .. S - 1)
         for (int i = 0; i < S; ++i)
           for (int j = 0; j < S; ++j) {
             const int ord = i + j;
             if (ord < 2 || ord > S - 1) continue;
-            mma_bf16(tmem + 3 * OZ_BN, da(i), db(j), OZ_IDESC, started3 ? 1u : 0u);
+            mma_bf16(tmem + 3 * BN, da(i), db(j), IDESC, started3 ? 1u : 0u);
             started3 = true;
           }
       }
@@ -259,6 +267,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     if (fail)           // let the loads still in flight land before the CTA leaves
       for (int q = consumed; q < issued; ++q) mbar_wait(&full[q % NST], (uint32_t)((q / NST) & 1), max_spin);
   }
+  if (tid < BN) s_eb[tid] = n0 + tid < d->N ? d->eb[n0 + tid] : 0;
   if (!mbar_wait(accb, 0, max_spin)) fail = 1;
   tc_fence_after();
   if (fail) {
@@ -267,43 +276,54 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
   }
   __syncthreads();
   if (!s_fail) {
+    // The stage area is free once every MMA has completed: stage the tile there
+    // as (hi, lo) rows (padded by one element against bank conflicts), then each
+    // warp stores its 32 rows with consecutive lanes on consecutive columns.
+    float2* stg = reinterpret_cast<float2*>(smem);
+    constexpr int SLD = BN + 1;
     const int row = m0 + warp * 32 + lane;
     const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
     const bool has3 = S >= 3;
     const int era = row < d->M ? d->ea[row] : 0;
+    float2* srow = stg + (warp * 32 + lane) * SLD;
 #pragma unroll 1
-    for (int c0 = 0; c0 < OZ_BN; c0 += 16) {
+    for (int c0 = 0; c0 < BN; c0 += 16) {
       uint32_t v0[16], v1[16], v2[16], v3[16];
-      tmem_ld16(lane_base + 0 * OZ_BN + c0, v0);
-      tmem_ld16(lane_base + 1 * OZ_BN + c0, v1);
-      tmem_ld16(lane_base + 2 * OZ_BN + c0, v2);
-      tmem_ld16(lane_base + 3 * OZ_BN + c0, v3);
+      tmem_ld16(lane_base + 0 * BN + c0, v0);
+      tmem_ld16(lane_base + 1 * BN + c0, v1);
+      tmem_ld16(lane_base + 2 * BN + c0, v2);
+      tmem_ld16(lane_base + 3 * BN + c0, v3);
       tmem_wait_ld();
-      if (row < d->M) {
-        float2* crow = d->C + (long long)row * d->ldc;
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const int n = n0 + c0 + j;
-          if (n >= d->N) continue;
-          float s, e, e2;
-          two_sum(__uint_as_float(v0[j]), __uint_as_float(v1[j]), s, e);
-          two_sum(s, __uint_as_float(v2[j]), s, e2);
-          e += e2;
-          if (has3) e += __uint_as_float(v3[j]);
-          const float h = s + e;
-          const float l = e - (h - s);
-          const int ex = era + d->eb[n];
-          const float s1 = pow2f(ex / 2), s2 = pow2f(ex - ex / 2);
-          crow[(long long)(n / d->cg) * d->cld + (n % d->cg)] = make_float2(h * s1 * s2, l * s1 * s2);
-        }
+      for (int j = 0; j < 16; ++j) {
+        float s, e, e2;
+        two_sum(__uint_as_float(v0[j]), __uint_as_float(v1[j]), s, e);
+        two_sum(s, __uint_as_float(v2[j]), s, e2);
+        e += e2;
+        if (has3) e += __uint_as_float(v3[j]);
+        const float h = s + e;
+        const float l = e - (h - s);
+        const int ex = era + s_eb[c0 + j];
+        const float s1 = pow2f(ex / 2), s2 = pow2f(ex - ex / 2);
+        srow[c0 + j] = make_float2(h * s1 * s2, l * s1 * s2);
       }
+    }
+    __syncwarp();
+    const int ncols = min(BN, d->N - n0);
+#pragma unroll 1
+    for (int rr = 0; rr < 32; ++rr) {
+      const int grow = m0 + warp * 32 + rr;
+      if (grow >= d->M) break;
+      float2* crow = d->C + (long long)grow * d->ldc + n0;
+      const float2* sr = stg + (warp * 32 + rr) * SLD;
+      for (int cc = lane; cc < ncols; cc += 32) crow[cc] = sr[cc];
     }
   }
   tc_fence_before();
   __syncthreads();
   if (warp == 0) {
     tc_fence_after();
-    tmem_dealloc(tmem, OZ_TMEM_COLS);
+    tmem_dealloc(tmem, TMEM_COLS);
   }
 }
 #endif

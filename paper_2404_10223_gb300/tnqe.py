@@ -34,12 +34,13 @@ class tnqe_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("chi_rot", ctypes.c_int), ("cutoff", ctypes.c_double),
                 ("solve_eps", ctypes.c_double), ("renormalize_rotated", ctypes.c_int),
                 ("max_jacobi_sweeps", ctypes.c_int), ("max_spin", ctypes.c_longlong),
-                ("cuda_stream", ctypes.c_void_p), ("device", ctypes.c_int)]
+                ("cuda_stream", ctypes.c_void_p), ("device", ctypes.c_int), ("use_graphs", ctypes.c_int)]
 
 
 EXPORTED = ["tnqe_default_options", "tnqe_create", "tnqe_add_mps", "tnqe_reset_mps", "tnqe_rotate",
             "tnqe_get_rotated", "tnqe_matrix_elements", "tnqe_solve", "tnqe_set_precision", "tnqe_last_timing", "tnqe_last_profile", "tnqe_apply_gate_noalloc",
-            "tnqe_last_error", "tnqe_destroy"]
+            "tnqe_autotune", "tnqe_set_tuning", "tnqe_clear_graphs", "tnqe_graph_count", "tnqe_last_error",
+            "tnqe_destroy"]
 
 _lib = None
 
@@ -66,6 +67,10 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.tnqe_last_profile.argtypes = [P, P, I]
     lib.tnqe_apply_gate_noalloc.argtypes = [P, P, I, I, I, P, P, P, D, D, I, I, D, I, P, P, P,
                                             ctypes.POINTER(I), ctypes.POINTER(D), P, ctypes.c_char_p, I]
+    lib.tnqe_autotune.argtypes = [P, P, I, P, P]
+    lib.tnqe_set_tuning.argtypes = [P, I, I, I]
+    lib.tnqe_clear_graphs.argtypes = [P]
+    lib.tnqe_graph_count.argtypes = [P]
     lib.tnqe_last_error.argtypes = [P]
     lib.tnqe_last_error.restype = ctypes.c_char_p
     lib.tnqe_destroy.argtypes = [P]
@@ -181,6 +186,27 @@ def tnqe_last_profile(ctx) -> np.ndarray:
     return p
 
 
+def tnqe_autotune(ctx, pairs):
+    """Tune the sliced-BF16 launch shapes on `pairs`; returns ((bn1, bn3, spmm_bw), 3x3 candidate times in ms)."""
+    pr = np.ascontiguousarray(np.asarray(pairs, dtype=np.int32).reshape(-1, 2))
+    cfg = np.zeros(3, dtype=np.int32)
+    times = np.zeros(9)
+    _check(ctx, load().tnqe_autotune(ctx, _ptr(pr), len(pr), _ptr(cfg), _ptr(times)))
+    return tuple(int(x) for x in cfg), times.reshape(3, 3)
+
+
+def tnqe_set_tuning(ctx, bn1: int, bn3: int, spmm_bw: int):
+    _check(ctx, load().tnqe_set_tuning(ctx, bn1, bn3, spmm_bw))
+
+
+def tnqe_clear_graphs(ctx):
+    _check(ctx, load().tnqe_clear_graphs(ctx))
+
+
+def tnqe_graph_count(ctx) -> int:
+    return int(load().tnqe_graph_count(ctx))
+
+
 def tnqe_apply_gate_noalloc(A: int, B: int, chi_l: int, chi_m: int, chi_r: int, q_l, q_m, q_r, c: float,
                             s: float, sigma_side: int, chi_max: int, cutoff: float, max_sweeps: int,
                             A_out: int, B_out: int, stream: int = 0):
@@ -243,6 +269,18 @@ class Context:
 
     def last_profile(self):
         return tnqe_last_profile(self.ctx)
+
+    def autotune(self, pairs):
+        return tnqe_autotune(self.ctx, pairs)
+
+    def set_tuning(self, bn1: int, bn3: int, spmm_bw: int):
+        tnqe_set_tuning(self.ctx, bn1, bn3, spmm_bw)
+
+    def clear_graphs(self):
+        tnqe_clear_graphs(self.ctx)
+
+    def graph_count(self) -> int:
+        return tnqe_graph_count(self.ctx)
 
     def close(self):
         if self.ctx:
