@@ -120,7 +120,11 @@ tnqe_status tnqe_rotate(tnqe_ctx* ctx, int i, int j, double* discarded_weight);
 tnqe_status tnqe_get_rotated(tnqe_ctx* ctx, int* bond_dims, double* tensors, long long max_doubles);
 
 /* H_ij and S_ij (Eq. 10) for npairs pairs.  pairs: 2*npairs ints (host),
- * (i, j) with i <= j.  H_out, S_out: npairs doubles each, host or device.
+ * (i, j) in either order: state i is the bra (the contraction runs in basis
+ * i) and state j the rotated ket.  Without truncation H_ij = H_ji; with it
+ * the two orders differ by the truncation error, so a caller assembling a
+ * symmetric matrix picks one order per pair and keeps it (tnqe_solve reads
+ * the upper triangle).  H_out, S_out: npairs doubles each, host or device.
  * Every pair is recomputed (rotation and contraction) on each call.
  *
  * One call puts all pairs' rotations (one launch) and contractions (a few

@@ -1618,7 +1618,6 @@ tnqe_status tnqe_matrix_elements(tnqe_ctx* c, const int* pairs, int npairs, doub
     for (int p = 0; p < npairs; ++p) {
       const int i = pairs[2 * p], j = pairs[2 * p + 1];
       if (i < 0 || j < 0 || i >= M || j >= M) throw Error(TNQE_ERR_STATE, "unknown MPS id in pair list");
-      if (i > j) throw Error(TNQE_ERR_ARG, "pairs must have i <= j");
       pl[p] = {i, j};
     }
     c->kept_pair_valid = 0;

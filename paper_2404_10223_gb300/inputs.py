@@ -262,3 +262,17 @@ def determinant_mps(N: int, occ_alpha: Sequence[int], occ_beta: Sequence[int]) -
         t[0, k, 0] = 1.0
         ts.append(t)
     return ts
+
+
+# ----------------------------------------------------------------------------- rotation-proposal network
+def draw_mlp_params(rng: np.random.Generator, n_in: int, n_h: int, n_out: int, out_scale: float = 0.1) -> np.ndarray:
+    """Initial parameters of the proposal network, flat FP32 in the order W1, b1, W2, b2, W3, b3.
+
+    He-style normal weights (variance 2 / fan_in) on the hidden layers, a
+    small output layer (the first proposals stay close to "no change"), zero
+    biases.
+    """
+    parts = [rng.normal(0.0, math.sqrt(2.0 / n_in), (n_h, n_in)), np.zeros(n_h),
+             rng.normal(0.0, math.sqrt(2.0 / n_h), (n_h, n_h)), np.zeros(n_h),
+             rng.normal(0.0, out_scale * math.sqrt(1.0 / n_h), (n_out, n_h)), np.zeros(n_out)]
+    return np.concatenate([np.ravel(x) for x in parts]).astype(np.float32)

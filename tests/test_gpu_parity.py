@@ -359,3 +359,14 @@ def test_sliced_bf16_ragged_and_tiny_chains():
                 g.add_mps(t, U)
             HG, SG = g.matrix_elements([(0, 0), (0, 1), (1, 1)])
         assert np.abs(HG - HA).max() <= 1e-9 and np.abs(SG - SA).max() <= 1e-10
+
+
+def test_reversed_pair_order_matches_oracle():
+    """(j, i) puts state j in the bra: equal to (i, j) up to truncation, and to the oracle's (j, i) exactly."""
+    w = inputs.workload("n10_chi32")
+    pairs = [(3, 1), (1, 3), (5, 0), (0, 5), (4, 4)]
+    o = oracle_ctx(w)
+    HB, SB = o.matrix_elements(pairs)
+    with gpu_ctx(w) as g:
+        HG, SG = g.matrix_elements(pairs)
+    assert np.abs(HG - HB).max() <= TOL_HS and np.abs(SG - SB).max() <= TOL_HS

@@ -1,5 +1,5 @@
 """CPU-only checks of the C ABI library: it builds for sm_103a, loads, and
-exports every entry point that include/tnqe.h declares (no compute calls)."""
+exports every entry point that include/*.h declares (no compute calls)."""
 import os
 import re
 import subprocess
@@ -10,7 +10,7 @@ from paper_2404_10223_gb300 import build as B
 from paper_2404_10223_gb300 import tnqe
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-HEADER = os.path.join(ROOT, "include", "tnqe.h")
+HEADERS = [os.path.join(ROOT, "include", f) for f in sorted(os.listdir(os.path.join(ROOT, "include"))) if f.endswith(".h")]
 
 
 @pytest.fixture(scope="module")
@@ -21,15 +21,18 @@ def lib_path():
 
 
 def declared_functions():
-    text = open(HEADER).read()
-    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(tnqe_[a-z_0-9]+)\s*\(", text)))
+    names = set()
+    for h in HEADERS:
+        text = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        names |= set(re.findall(r"\b(tnqe_[a-z_0-9]+)\s*\(", text))
+    return sorted(names)
 
 
 def test_header_declares_the_abi():
     names = declared_functions()
     for n in ["tnqe_create", "tnqe_add_mps", "tnqe_rotate", "tnqe_matrix_elements", "tnqe_solve",
-              "tnqe_last_error", "tnqe_destroy"]:
+              "tnqe_last_error", "tnqe_destroy", "tnqe_mlp_create", "tnqe_mlp_forward", "tnqe_mlp_gradient",
+              "tnqe_mlp_adam_step"]:
         assert n in names
 
 
@@ -45,6 +48,9 @@ def test_binding_loads_and_resolves(lib_path):
     for n in declared_functions():
         assert getattr(lib, n) is not None
     assert set(tnqe.EXPORTED) <= set(declared_functions())
+    from paper_2404_10223_gb300 import mlp
+    assert set(mlp.EXPORTED) <= set(declared_functions())
+    mlp.load(lib_path)
 
 
 def test_default_options_without_gpu(lib_path):
