@@ -192,6 +192,8 @@ def run_native(args):
     tnqe.load()
     w = inputs.workload(args.workload)
     pairs = w.all_pairs()
+    if args.max_pairs > 0:                # a smaller case of the same workload (profiling captures)
+        pairs = pairs[:args.max_pairs]
     npairs = len(pairs)
     stream = torch.cuda.Stream()
     g = tnqe.Context(w.h1, w.eri, w.N, w.n_alpha, w.n_beta, cutoff=w.cutoff, precision=PREC[args.precision],
@@ -199,7 +201,7 @@ def run_native(args):
     for m in w.mps:
         g.add_mps(m.tensors, m.U)
     tuned = None
-    if args.precision.startswith("bf16"):
+    if args.precision.startswith("bf16") and not args.no_autotune:
         tuned, _ = g.autotune(pairs)      # launch shapes, chosen outside the timed region
     Hd = torch.zeros(npairs, dtype=torch.float64, device="cuda")
     Sd = torch.zeros(npairs, dtype=torch.float64, device="cuda")
@@ -322,7 +324,7 @@ def run_native(args):
         pinned.append((ts, U))
         h2d += sum(t.numel() * 8 for t in ts) + U.numel() * 8
     e2e_ms = []
-    for it in range(max(1, min(args.steps, 3)) + 1):
+    for it in range(0 if args.no_e2e else max(1, min(args.steps, 3)) + 1):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         g.reset_mps()
@@ -332,11 +334,12 @@ def run_native(args):
         torch.cuda.synchronize()
         if it > 0:
             e2e_ms.append(1000.0 * (time.perf_counter() - t0))
-    e2e_v = npairs * world / (max_over_ranks(statistics.mean(e2e_ms), world) / 1000.0)
+    e2e_v = npairs * world / (max_over_ranks(statistics.mean(e2e_ms), world) / 1000.0) if e2e_ms else None
     launches = int(prof[9])
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
             "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": DTYPE[args.precision], "data": "synthetic", "config": config_of(w, args.precision),
+            "dtype": DTYPE[args.precision], "data": "synthetic",
+            "config": {**config_of(w, args.precision), "pairs": npairs},
             "clocks": clk, "gpu_launches": launches,
             "graph": {"replayed": replayed, "tuned_shapes": tuned},
             "e2e": {"value": e2e_v, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": 16 * npairs},
@@ -361,6 +364,9 @@ def main():
     ap.add_argument("--precision", default="bf16x15", choices=list(PREC))
     ap.add_argument("--fp64-steps", type=int, default=2, help="timed steps of the plain FP64 form (0 = skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--max-pairs", type=int, default=0, help="use only the first K pairs (profiling on a small case)")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-buffer leg")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes (profiling)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -172,6 +172,23 @@ int tnqe_graph_count(const tnqe_ctx* ctx);
 tnqe_status tnqe_solve(tnqe_ctx* ctx, const double* H, const double* S, int M,
                        double* E, double* C, int* rank_kept, double* kappa1);
 
+/* tnqe_solve with the eigenvalue threshold of S given per call: keep
+ * eigenvalues above eps * lambda_max (0 <= eps < 1).  eps = solve_eps is
+ * tnqe_solve; eps = sqrt(DBL_EPSILON) is the pseudo-inverse tolerance
+ * sqrt(eps_mach) |S| the paper uses for its inversion variant (Sec. IV C):
+ * both variants span the same eigenvectors of S and differ in this threshold. */
+tnqe_status tnqe_solve_ex(tnqe_ctx* ctx, const double* H, const double* S, int M, double eps,
+                          double* E, double* C, int* rank_kept, double* kappa1);
+
+/* Linear-dependence residuals of a subspace (the discard test of Sec. IV C):
+ * residuals[j] = S_jj - s_j^T (S_<j)^+ s_j, s_j = S[0:j, j], S_<j = S[0:j, 0:j],
+ * the pseudo-inverse keeping eigenvalues above eps * lambda_max.  It is the
+ * squared norm of state j's component outside the span of states 0..j-1
+ * (residuals[0] = S_00).  A state whose residual falls below a threshold
+ * (1e-3 in the paper's discussion) adds nothing new and may be discarded.
+ * S: M*M row-major host, upper triangle used, M <= 32; residuals: M doubles (host). */
+tnqe_status tnqe_dependence(tnqe_ctx* ctx, const double* S, int M, double eps, double* residuals);
+
 /* Change the contraction precision (tnqe_precision) of later calls. */
 tnqe_status tnqe_set_precision(tnqe_ctx* ctx, int precision);
 

@@ -160,6 +160,7 @@ struct tnqe_ctx {
   DBuf con_ws, con_desc, con_out;
   DBuf tc_ws, tc_desc, tc_err;
   DBuf oz_ws, oz_desc;
+  DBuf solve_buf;                          // tnqe_solve / tnqe_dependence, sized once for M = 32
   // graph capture / replay of whole matrix-element calls
   bool capturing = false;
   std::vector<Upload>* cap_uploads = nullptr;
@@ -1008,6 +1009,9 @@ void run_contractions_oz(tnqe_ctx* c, const std::vector<std::pair<int, int>>& pa
     int spmm_bw = spmm_df_smem_width(max_ncx);
     if (c->tune.spmm_bw > 0 && spmm_bw > 0) spmm_bw = std::min(spmm_bw, c->tune.spmm_bw);
     const int bn1 = c->tune.oz_bn1, bn3 = c->tune.oz_bn3;
+    std::vector<int> maxK3(N, 4);                 // largest stage-3 K (4 chi_a) per site over the wave
+    for (int w = 0; w < nw; ++w)
+      for (int t = 0; t < N; ++t) maxK3[t] = std::max(maxK3[t], 4 * c->mps[pairs[p0 + w].first]->dims[t]);
     std::vector<SliceRowsDesc> sa;
     std::vector<SliceColsDesc> sb;
     std::vector<OzGemmDesc> g1, g3;
@@ -1151,7 +1155,8 @@ void run_contractions_oz(tnqe_ctx* c, const std::vector<std::pair<int, int>>& pa
       else
         CKL(launch_spmm_df(reinterpret_cast<SpmmDfDesc*>(dd + o_sp) + i, pre(o_spp), nw, sppre[ip + nw], c->stream));
       record_event(c, E[3]);
-      CKL(launch_slice_cols(reinterpret_cast<SliceColsDesc*>(dd + o_sb) + i, pre(o_sbp), nw, sbpre[ip + nw], c->stream));
+      CKL(launch_slice_cols(reinterpret_cast<SliceColsDesc*>(dd + o_sb) + i, pre(o_sbp), nw, sbpre[ip + nw],
+                            maxK3[t], c->stream));
       record_event(c, E[4]);
       CKL(launch_gemm_bf16s(reinterpret_cast<OzGemmDesc*>(dd + o_g3) + i, pre(o_g3p), nw, g3pre[ip + nw],
                             c->opt.max_spin, derr, bn3, c->stream));
@@ -1736,15 +1741,15 @@ tnqe_status tnqe_clear_graphs(tnqe_ctx* c) {
 
 int tnqe_graph_count(const tnqe_ctx* c) { return c ? (int)c->graphs.size() : 0; }
 
-tnqe_status tnqe_solve(tnqe_ctx* c, const double* H, const double* S, int M, double* E, double* C, int* rank_kept,
-                       double* kappa1) {
+tnqe_status tnqe_solve_ex(tnqe_ctx* c, const double* H, const double* S, int M, double eps, double* E, double* C,
+                          int* rank_kept, double* kappa1) {
   try {
     check_ctx(c);
     if (M < 1 || M > 32 || !H || !S || !E || !C || !rank_kept || !kappa1) throw Error(TNQE_ERR_ARG, "bad solve arguments");
-    DBuf buf;
+    if (!(eps >= 0.0) || eps >= 1.0) throw Error(TNQE_ERR_ARG, "eps must be in [0, 1)");
     const size_t mm = (size_t)M * M;
-    buf.ensure(sizeof(double) * (3 * mm + M + 2) + 16);
-    double* dH = buf.as<double>();
+    c->solve_buf.ensure(sizeof(double) * (3 * 32 * 32 + 32 + 2) + 16);   // sized for M = 32 once
+    double* dH = c->solve_buf.as<double>();
     double* dS = dH + mm;
     double* dC = dS + mm;
     double* dE = dC + mm;
@@ -1753,7 +1758,7 @@ tnqe_status tnqe_solve(tnqe_ctx* c, const double* H, const double* S, int M, dou
     int* dSt = dR + 1;
     CK(cudaMemcpyAsync(dH, H, sizeof(double) * mm, cudaMemcpyHostToDevice, c->stream));
     CK(cudaMemcpyAsync(dS, S, sizeof(double) * mm, cudaMemcpyHostToDevice, c->stream));
-    CKL(launch_solve(dH, dS, M, c->opt.solve_eps, c->opt.max_jacobi_sweeps, dE, dC, dR, dK, dSt, c->stream));
+    CKL(launch_solve(dH, dS, M, eps, c->opt.max_jacobi_sweeps, dE, dC, dR, dK, dSt, c->stream));
     int st = 0;
     CK(cudaMemcpyAsync(E, dE, sizeof(double) * M, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaMemcpyAsync(C, dC, sizeof(double) * mm, cudaMemcpyDeviceToHost, c->stream));
@@ -1761,7 +1766,36 @@ tnqe_status tnqe_solve(tnqe_ctx* c, const double* H, const double* S, int M, dou
     CK(cudaMemcpyAsync(kappa1, dK, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     CK(cudaMemcpyAsync(&st, dSt, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
-    buf.release();
+    if (st) throw Error(TNQE_ERR_NOCONV, "eigensolver hit the sweep limit");
+    return TNQE_OK;
+  } catch (const Error& e) {
+    return fail(c, e);
+  }
+}
+
+tnqe_status tnqe_solve(tnqe_ctx* c, const double* H, const double* S, int M, double* E, double* C, int* rank_kept,
+                       double* kappa1) {
+  if (!c) return TNQE_ERR_ARG;
+  return tnqe_solve_ex(c, H, S, M, c->opt.solve_eps, E, C, rank_kept, kappa1);
+}
+
+tnqe_status tnqe_dependence(tnqe_ctx* c, const double* S, int M, double eps, double* residuals) {
+  try {
+    check_ctx(c);
+    if (M < 1 || M > 32 || !S || !residuals) throw Error(TNQE_ERR_ARG, "bad dependence arguments");
+    if (!(eps >= 0.0) || eps >= 1.0) throw Error(TNQE_ERR_ARG, "eps must be in [0, 1)");
+    const size_t mm = (size_t)M * M;
+    c->solve_buf.ensure(sizeof(double) * (3 * 32 * 32 + 32 + 2) + 16);
+    double* dS = c->solve_buf.as<double>();
+    double* dR = dS + mm;
+    int* dSt = reinterpret_cast<int*>(dR + M);
+    CK(cudaMemcpyAsync(dS, S, sizeof(double) * mm, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemsetAsync(dSt, 0, sizeof(int), c->stream));
+    CKL(launch_dependence(dS, M, eps, c->opt.max_jacobi_sweeps, dR, dSt, c->stream));
+    int st = 0;
+    CK(cudaMemcpyAsync(residuals, dR, sizeof(double) * M, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(&st, dSt, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
     if (st) throw Error(TNQE_ERR_NOCONV, "eigensolver hit the sweep limit");
     return TNQE_OK;
   } catch (const Error& e) {
@@ -1816,6 +1850,7 @@ void tnqe_destroy(tnqe_ctx* c) {
   c->tc_err.release();
   c->oz_ws.release();
   c->oz_desc.release();
+  c->solve_buf.release();
   c->graphs.clear();
   for (auto& e : c->ev)
     if (e) cudaEventDestroy(e);

@@ -98,24 +98,30 @@ __global__ void __launch_bounds__(256) slice_rows_kernel(const SliceRowsDesc* __
 }
 
 // Columns (w',b') of Y[(a,k)][(w',b')] over K = (a,k), transposed to K-major slices.
-// One CTA per 16 columns of one problem; 256 threads.
+// One CTA per 16 columns of one problem, 256 threads.  The whole K x 16 block
+// is read once into shared memory (rows padded to 17 elements), its column
+// maxima taken on the way, then sliced column by column.
+constexpr int SLC_W = 16, SLC_LD = SLC_W + 1;
 __global__ void __launch_bounds__(256) slice_cols_kernel(const SliceColsDesc* __restrict__ descs,
                                                          const long long* __restrict__ prefix, int nprob) {
-  __shared__ float2 tile[64][17];
-  __shared__ float red[16][17];
-  __shared__ int sexp[16];
+  extern __shared__ float2 blk[];                // [K][SLC_LD]
+  __shared__ float red[16][SLC_W + 1];
+  __shared__ int sexp[SLC_W];
   const long long task = blockIdx.x;
   const int p = find_prob(prefix, nprob, task);
   const SliceColsDesc& d = descs[p];
-  const int c0 = (int)(task - prefix[p]) * 16;
+  const int c0 = (int)(task - prefix[p]) * SLC_W;
   const int tid = threadIdx.x, cc = tid & 15, rr = tid >> 4;   // 16 columns x 16 row groups
   const int col = c0 + cc;
   float m = 0.f;
-  if (col < d.ncols)
-    for (int k = rr; k < d.K; k += 16) m = fmaxf(m, fabsf(d.src[(long long)k * d.ld + col].x));
+  for (int k = rr; k < d.K; k += 16) {
+    const float2 v = col < d.ncols ? d.src[(long long)k * d.ld + col] : make_float2(0.f, 0.f);
+    blk[k * SLC_LD + cc] = v;
+    m = fmaxf(m, fabsf(v.x));
+  }
   red[rr][cc] = m;
   __syncthreads();
-  if (tid < 16) {
+  if (tid < SLC_W) {
     float mm = 0.f;
     for (int i = 0; i < 16; ++i) mm = fmaxf(mm, red[i][tid]);
     const int e = row_exponent_f(mm);
@@ -123,22 +129,15 @@ __global__ void __launch_bounds__(256) slice_cols_kernel(const SliceColsDesc* __
     if (c0 + tid < d.ncols) d.exps[c0 + tid] = e;
   }
   __syncthreads();
-  // writer mapping: column wc = tid / 16, four consecutive k per thread
-  const int wc = tid >> 4, wk = (tid & 15) * 4;
-  for (int k0 = 0; k0 < d.K; k0 += 64) {
-    for (int i = tid; i < 64 * 16; i += 256) {
-      const int k = k0 + (i >> 4), c = c0 + (i & 15);
-      tile[i >> 4][i & 15] = (k < d.K && c < d.ncols) ? d.src[(long long)k * d.ld + c] : make_float2(0.f, 0.f);
+  // writers: a warp takes two columns, consecutive lanes consecutive k
+  const int wc = tid >> 4, wl = tid & 15;
+  if (c0 + wc < d.ncols) {
+    __nv_bfloat16* dst = d.dst + (long long)(c0 + wc) * d.ldK;
+    const int e = sexp[wc];
+    for (int k = wl; k < d.K; k += 16) {
+      const float2 v = blk[k * SLC_LD + wc];
+      slice_df(v.x, v.y, e, d.ns, dst + k, d.slice_stride);
     }
-    __syncthreads();
-    if (c0 + wc < d.ncols) {
-      __nv_bfloat16* dst = d.dst + (long long)(c0 + wc) * d.ldK;
-      for (int u = 0; u < 4; ++u) {
-        const int k = k0 + wk + u;
-        if (k < d.K) slice_df(tile[wk + u][wc].x, tile[wk + u][wc].y, sexp[wc], d.ns, dst + k, d.slice_stride);
-      }
-    }
-    __syncthreads();
   }
 }
 
@@ -233,9 +232,9 @@ __global__ void __launch_bounds__(256, 2) spmm_df_smem_kernel(const SpmmDfDesc* 
     xs[i] = (b0 + c < d.width) ? Xa[(long long)r * d.width + c] : make_float2(0.f, 0.f);
   }
   __syncthreads();
-  // each thread: one row, columns c and c + BW/2 (two independent accumulations)
-  constexpr int HW = BW > 1 ? BW / 2 : 1;
-  constexpr int NC = BW > 1 ? 2 : 1;
+  // each thread: one row, NC columns c, c + HW, ... (independent accumulations, shared index loads)
+  constexpr int NC = BW < 4 ? BW : 4;
+  constexpr int HW = BW / NC;
   const int c = tid % HW;
   float2* Ya = d.Y + (long long)a * d.nrows * d.width + b0;
   for (int r0 = 0; r0 < d.nrows; r0 += 256 / HW) {
@@ -289,9 +288,14 @@ int launch_slice_rows(const SliceRowsDesc* d, const long long* prefix, int n, lo
   slice_rows_kernel<<<(unsigned)((rows + 7) / 8), 256, 0, (cudaStream_t)stream>>>(d, prefix, n, rows);
   return (int)cudaGetLastError();
 }
-int launch_slice_cols(const SliceColsDesc* d, const long long* prefix, int n, long long blocks, void* stream) {
+int launch_slice_cols(const SliceColsDesc* d, const long long* prefix, int n, long long blocks, int max_k,
+                      void* stream) {
   if (blocks <= 0) return 0;
-  slice_cols_kernel<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(d, prefix, n);
+  const size_t smem = (size_t)max_k * SLC_LD * sizeof(float2);
+  if (smem > 200 * 1024) return (int)cudaErrorInvalidValue;
+  const cudaError_t e = cudaFuncSetAttribute(slice_cols_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return (int)e;
+  slice_cols_kernel<<<(unsigned)blocks, 256, smem, (cudaStream_t)stream>>>(d, prefix, n);
   return (int)cudaGetLastError();
 }
 int launch_slice_sites(const SliceSiteDesc* d, const long long* prefix, int n, long long rows, void* stream) {

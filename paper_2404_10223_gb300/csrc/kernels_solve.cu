@@ -171,7 +171,48 @@ __global__ void solve_kernel(const double* __restrict__ Hin, const double* __res
   }
 }
 
+// Linear-dependence residuals (Sec. IV C's discard test): warp j computes
+// r_j = S_jj - s^T S_<j^+ s with s = S[0:j, j] and S_<j = S[0:j, 0:j], the
+// pseudo-inverse keeping eigenvalues above eps * lambda_max.  r_j is the
+// squared norm of state j's component outside the span of states 0..j-1.
+__global__ void dependence_kernel(const double* __restrict__ Sin, int M, double eps, int max_sweeps,
+                                  double* __restrict__ resid, int* __restrict__ status) {
+  __shared__ double A[MS][MS + 1], V[MS][MS + 1];
+  __shared__ double sv[MS];
+  const int j = blockIdx.x, lane = threadIdx.x;
+  if (j >= M) return;
+  for (int r = 0; r < j; ++r)
+    if (lane < j) {
+      const int a = r < lane ? r : lane, b = r < lane ? lane : r;   // upper triangle is authoritative
+      A[r][lane] = Sin[a * M + b];
+    }
+  if (lane < j) sv[lane] = Sin[lane * M + j];
+  __syncwarp();
+  int st = 0;
+  if (j > 0) st = warp_jacobi_eig(A, V, j, max_sweeps);
+  __syncwarp();
+  if (lane == 0) {
+    double lmax = 0.0;
+    for (int k = 0; k < j; ++k) lmax = fmax(lmax, A[k][k]);
+    double proj = 0.0;
+    for (int k = 0; k < j; ++k) {
+      if (!(A[k][k] > eps * lmax)) continue;
+      double wk = 0.0;
+      for (int r = 0; r < j; ++r) wk = fma(V[r][k], sv[r], wk);
+      proj += wk * wk / A[k][k];
+    }
+    resid[j] = Sin[j * M + j] - proj;
+    if (st) atomicOr(status, STATUS_NOCONV);
+  }
+}
+
 }  // namespace
+
+int launch_dependence(const double* d_S, int M, double eps, int max_sweeps, double* d_resid, int* d_status,
+                      void* stream) {
+  dependence_kernel<<<M, 32, 0, (cudaStream_t)stream>>>(d_S, M, eps, max_sweeps, d_resid, d_status);
+  return (int)cudaGetLastError();
+}
 
 int launch_solve(const double* d_H, const double* d_S, int M, double eps, int max_sweeps, double* d_E, double* d_C,
                  int* d_rank, double* d_kappa, int* d_status, void* stream) {

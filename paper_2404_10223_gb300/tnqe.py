@@ -39,7 +39,7 @@ class tnqe_options(ctypes.Structure):
 
 EXPORTED = ["tnqe_default_options", "tnqe_create", "tnqe_add_mps", "tnqe_reset_mps", "tnqe_rotate",
             "tnqe_get_rotated", "tnqe_matrix_elements", "tnqe_solve", "tnqe_set_precision", "tnqe_last_timing", "tnqe_last_profile", "tnqe_apply_gate_noalloc",
-            "tnqe_autotune", "tnqe_set_tuning", "tnqe_clear_graphs", "tnqe_graph_count", "tnqe_last_error",
+            "tnqe_solve_ex", "tnqe_dependence", "tnqe_autotune", "tnqe_set_tuning", "tnqe_clear_graphs", "tnqe_graph_count", "tnqe_last_error",
             "tnqe_destroy"]
 
 _lib = None
@@ -67,6 +67,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.tnqe_last_profile.argtypes = [P, P, I]
     lib.tnqe_apply_gate_noalloc.argtypes = [P, P, I, I, I, P, P, P, D, D, I, I, D, I, P, P, P,
                                             ctypes.POINTER(I), ctypes.POINTER(D), P, ctypes.c_char_p, I]
+    lib.tnqe_solve_ex.argtypes = [P, P, P, I, D, P, P, ctypes.POINTER(I), ctypes.POINTER(D)]
+    lib.tnqe_dependence.argtypes = [P, P, I, D, P]
     lib.tnqe_autotune.argtypes = [P, P, I, P, P]
     lib.tnqe_set_tuning.argtypes = [P, I, I, I]
     lib.tnqe_clear_graphs.argtypes = [P]
@@ -169,6 +171,23 @@ def tnqe_solve(ctx, H, S):
     return E, C, rank.value, k1.value
 
 
+def tnqe_solve_ex(ctx, H, S, eps: float):
+    H, S = _f64(H), _f64(S)
+    M = H.shape[0]
+    E, C = np.zeros(M), np.zeros((M, M))
+    rank, k1 = ctypes.c_int(), ctypes.c_double()
+    _check(ctx, load().tnqe_solve_ex(ctx, _ptr(H), _ptr(S), M, eps, _ptr(E), _ptr(C), ctypes.byref(rank),
+                                     ctypes.byref(k1)))
+    return E, C, rank.value, k1.value
+
+
+def tnqe_dependence(ctx, S, eps: float = 1e-12) -> np.ndarray:
+    S = _f64(S)
+    r = np.zeros(S.shape[0])
+    _check(ctx, load().tnqe_dependence(ctx, _ptr(S), S.shape[0], eps, _ptr(r)))
+    return r
+
+
 def tnqe_set_precision(ctx, precision: int):
     _check(ctx, load().tnqe_set_precision(ctx, precision))
 
@@ -260,6 +279,12 @@ class Context:
 
     def solve(self, H, S):
         return tnqe_solve(self.ctx, H, S)
+
+    def solve_ex(self, H, S, eps: float):
+        return tnqe_solve_ex(self.ctx, H, S, eps)
+
+    def dependence(self, S, eps: float = 1e-12):
+        return tnqe_dependence(self.ctx, S, eps)
 
     def set_precision(self, p: int):
         tnqe_set_precision(self.ctx, p)
