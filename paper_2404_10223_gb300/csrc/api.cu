@@ -1009,9 +1009,6 @@ void run_contractions_oz(tnqe_ctx* c, const std::vector<std::pair<int, int>>& pa
     int spmm_bw = spmm_df_smem_width(max_ncx);
     if (c->tune.spmm_bw > 0 && spmm_bw > 0) spmm_bw = std::min(spmm_bw, c->tune.spmm_bw);
     const int bn1 = c->tune.oz_bn1, bn3 = c->tune.oz_bn3;
-    std::vector<int> maxK3(N, 4);                 // largest stage-3 K (4 chi_a) per site over the wave
-    for (int w = 0; w < nw; ++w)
-      for (int t = 0; t < N; ++t) maxK3[t] = std::max(maxK3[t], 4 * c->mps[pairs[p0 + w].first]->dims[t]);
     std::vector<SliceRowsDesc> sa;
     std::vector<SliceColsDesc> sb;
     std::vector<OzGemmDesc> g1, g3;
@@ -1147,7 +1144,7 @@ void run_contractions_oz(tnqe_ctx* c, const std::vector<std::pair<int, int>>& pa
       CKL(launch_slice_rows(reinterpret_cast<SliceRowsDesc*>(dd + o_sa) + i, pre(o_sap), nw, sapre[ip + nw], c->stream));
       record_event(c, E[1]);
       CKL(launch_gemm_bf16s(reinterpret_cast<OzGemmDesc*>(dd + o_g1) + i, pre(o_g1p), nw, g1pre[ip + nw],
-                            c->opt.max_spin, derr, bn1, c->stream));
+                            c->opt.max_spin, derr, bn1, ns, c->stream));
       record_event(c, E[2]);
       if (spmm_bw)
         CKL(launch_spmm_df_smem(reinterpret_cast<SpmmDfDesc*>(dd + o_sp) + i, pre(o_spp), nw, sppre[ip + nw], spmm_bw,
@@ -1155,11 +1152,10 @@ void run_contractions_oz(tnqe_ctx* c, const std::vector<std::pair<int, int>>& pa
       else
         CKL(launch_spmm_df(reinterpret_cast<SpmmDfDesc*>(dd + o_sp) + i, pre(o_spp), nw, sppre[ip + nw], c->stream));
       record_event(c, E[3]);
-      CKL(launch_slice_cols(reinterpret_cast<SliceColsDesc*>(dd + o_sb) + i, pre(o_sbp), nw, sbpre[ip + nw],
-                            maxK3[t], c->stream));
+      CKL(launch_slice_cols(reinterpret_cast<SliceColsDesc*>(dd + o_sb) + i, pre(o_sbp), nw, sbpre[ip + nw], c->stream));
       record_event(c, E[4]);
       CKL(launch_gemm_bf16s(reinterpret_cast<OzGemmDesc*>(dd + o_g3) + i, pre(o_g3p), nw, g3pre[ip + nw],
-                            c->opt.max_spin, derr, bn3, c->stream));
+                            c->opt.max_spin, derr, bn3, ns, c->stream));
       record_event(c, E[5]);
       c->launches += 5;
     }

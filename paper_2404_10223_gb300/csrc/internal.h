@@ -171,8 +171,7 @@ int launch_gemm_tf32x3(const TcGemmDesc* d, const long long* tile_prefix, int np
 int launch_spmm_t_f32(const SpmmTDesc* d, const long long* prefix, int nprob, long long total, void* stream);
 int launch_extract_f32(const float* const* fin, int npairs, int ld, double* H, double* S, void* stream);
 int launch_slice_rows(const SliceRowsDesc* d, const long long* prefix, int n, long long rows, void* stream);
-int launch_slice_cols(const SliceColsDesc* d, const long long* prefix, int n, long long blocks, int max_k,
-                      void* stream);
+int launch_slice_cols(const SliceColsDesc* d, const long long* prefix, int n, long long blocks, void* stream);
 int launch_slice_sites(const SliceSiteDesc* d, const long long* prefix, int n, long long rows, void* stream);
 int launch_spmm_df(const SpmmDfDesc* d, const long long* prefix, int n, long long total, void* stream);
 // shared-memory form: one CTA per (problem, a, bw ket columns); prefix counts CTAs
@@ -184,7 +183,7 @@ int launch_unit_env_f64(double* const* env, int n, void* stream);
 int launch_unit_env_f32(float* const* env, int n, void* stream);
 int launch_extract_df(const float2* const* fin, int npairs, double* H, double* S, void* stream);
 int launch_gemm_bf16s(const OzGemmDesc* d, const long long* tile_prefix, int nprob, long long total_tiles,
-                      long long max_spin, int* err, int bn, void* stream);
+                      long long max_spin, int* err, int bn, int ns, void* stream);
 int launch_dependence(const double* d_S, int M, double eps, int max_sweeps, double* d_resid, int* d_status,
                       void* stream);
 int launch_solve(const double* d_H, const double* d_S, int M, double eps, int max_sweeps,

@@ -98,30 +98,24 @@ __global__ void __launch_bounds__(256) slice_rows_kernel(const SliceRowsDesc* __
 }
 
 // Columns (w',b') of Y[(a,k)][(w',b')] over K = (a,k), transposed to K-major slices.
-// One CTA per 16 columns of one problem, 256 threads.  The whole K x 16 block
-// is read once into shared memory (rows padded to 17 elements), its column
-// maxima taken on the way, then sliced column by column.
-constexpr int SLC_W = 16, SLC_LD = SLC_W + 1;
+// One CTA per 16 columns of one problem; 256 threads.
 __global__ void __launch_bounds__(256) slice_cols_kernel(const SliceColsDesc* __restrict__ descs,
                                                          const long long* __restrict__ prefix, int nprob) {
-  extern __shared__ float2 blk[];                // [K][SLC_LD]
-  __shared__ float red[16][SLC_W + 1];
-  __shared__ int sexp[SLC_W];
+  __shared__ float2 tile[64][17];
+  __shared__ float red[16][17];
+  __shared__ int sexp[16];
   const long long task = blockIdx.x;
   const int p = find_prob(prefix, nprob, task);
   const SliceColsDesc& d = descs[p];
-  const int c0 = (int)(task - prefix[p]) * SLC_W;
+  const int c0 = (int)(task - prefix[p]) * 16;
   const int tid = threadIdx.x, cc = tid & 15, rr = tid >> 4;   // 16 columns x 16 row groups
   const int col = c0 + cc;
   float m = 0.f;
-  for (int k = rr; k < d.K; k += 16) {
-    const float2 v = col < d.ncols ? d.src[(long long)k * d.ld + col] : make_float2(0.f, 0.f);
-    blk[k * SLC_LD + cc] = v;
-    m = fmaxf(m, fabsf(v.x));
-  }
+  if (col < d.ncols)
+    for (int k = rr; k < d.K; k += 16) m = fmaxf(m, fabsf(d.src[(long long)k * d.ld + col].x));
   red[rr][cc] = m;
   __syncthreads();
-  if (tid < SLC_W) {
+  if (tid < 16) {
     float mm = 0.f;
     for (int i = 0; i < 16; ++i) mm = fmaxf(mm, red[i][tid]);
     const int e = row_exponent_f(mm);
@@ -129,15 +123,22 @@ __global__ void __launch_bounds__(256) slice_cols_kernel(const SliceColsDesc* __
     if (c0 + tid < d.ncols) d.exps[c0 + tid] = e;
   }
   __syncthreads();
-  // writers: a warp takes two columns, consecutive lanes consecutive k
-  const int wc = tid >> 4, wl = tid & 15;
-  if (c0 + wc < d.ncols) {
-    __nv_bfloat16* dst = d.dst + (long long)(c0 + wc) * d.ldK;
-    const int e = sexp[wc];
-    for (int k = wl; k < d.K; k += 16) {
-      const float2 v = blk[k * SLC_LD + wc];
-      slice_df(v.x, v.y, e, d.ns, dst + k, d.slice_stride);
+  // writer mapping: column wc = tid / 16, four consecutive k per thread
+  const int wc = tid >> 4, wk = (tid & 15) * 4;
+  for (int k0 = 0; k0 < d.K; k0 += 64) {
+    for (int i = tid; i < 64 * 16; i += 256) {
+      const int k = k0 + (i >> 4), c = c0 + (i & 15);
+      tile[i >> 4][i & 15] = (k < d.K && c < d.ncols) ? d.src[(long long)k * d.ld + c] : make_float2(0.f, 0.f);
     }
+    __syncthreads();
+    if (c0 + wc < d.ncols) {
+      __nv_bfloat16* dst = d.dst + (long long)(c0 + wc) * d.ldK;
+      for (int u = 0; u < 4; ++u) {
+        const int k = k0 + wk + u;
+        if (k < d.K) slice_df(tile[wk + u][wc].x, tile[wk + u][wc].y, sexp[wc], d.ns, dst + k, d.slice_stride);
+      }
+    }
+    __syncthreads();
   }
 }
 
@@ -233,7 +234,7 @@ __global__ void __launch_bounds__(256, 2) spmm_df_smem_kernel(const SpmmDfDesc* 
   }
   __syncthreads();
   // each thread: one row, NC columns c, c + HW, ... (independent accumulations, shared index loads)
-  constexpr int NC = BW < 4 ? BW : 4;
+  constexpr int NC = BW < 2 ? BW : 2;
   constexpr int HW = BW / NC;
   const int c = tid % HW;
   float2* Ya = d.Y + (long long)a * d.nrows * d.width + b0;
@@ -288,14 +289,9 @@ int launch_slice_rows(const SliceRowsDesc* d, const long long* prefix, int n, lo
   slice_rows_kernel<<<(unsigned)((rows + 7) / 8), 256, 0, (cudaStream_t)stream>>>(d, prefix, n, rows);
   return (int)cudaGetLastError();
 }
-int launch_slice_cols(const SliceColsDesc* d, const long long* prefix, int n, long long blocks, int max_k,
-                      void* stream) {
+int launch_slice_cols(const SliceColsDesc* d, const long long* prefix, int n, long long blocks, void* stream) {
   if (blocks <= 0) return 0;
-  const size_t smem = (size_t)max_k * SLC_LD * sizeof(float2);
-  if (smem > 200 * 1024) return (int)cudaErrorInvalidValue;
-  const cudaError_t e = cudaFuncSetAttribute(slice_cols_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return (int)e;
-  slice_cols_kernel<<<(unsigned)blocks, 256, smem, (cudaStream_t)stream>>>(d, prefix, n);
+  slice_cols_kernel<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(d, prefix, n);
   return (int)cudaGetLastError();
 }
 int launch_slice_sites(const SliceSiteDesc* d, const long long* prefix, int n, long long rows, void* stream) {
@@ -363,24 +359,37 @@ int launch_extract_df(const float2* const* fin, int npairs, double* H, double* S
   extract_df_kernel<<<(npairs + 127) / 128, 128, 0, (cudaStream_t)stream>>>(fin, npairs, H, S);
   return (int)cudaGetLastError();
 }
+namespace {
+template <int BN, int S>
+int launch_bf16s(const OzGemmDesc* d, const long long* tile_prefix, int nprob, long long total_tiles,
+                 long long max_spin, int* err, cudaStream_t st) {
+  const cudaError_t e =
+      cudaFuncSetAttribute(gemm_bf16s_kernel<BN, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM_BYTES);
+  if (e != cudaSuccess) return (int)e;
+  gemm_bf16s_kernel<BN, S><<<(unsigned)total_tiles, OZ_THREADS, OZ_SMEM_BYTES, st>>>(d, tile_prefix, nprob, max_spin,
+                                                                                      err);
+  return (int)cudaGetLastError();
+}
+template <int BN>
+int launch_bf16s_s(const OzGemmDesc* d, const long long* tile_prefix, int nprob, long long total_tiles,
+                   long long max_spin, int* err, int ns, cudaStream_t st) {
+  switch (ns) {
+    case 2: return launch_bf16s<BN, 2>(d, tile_prefix, nprob, total_tiles, max_spin, err, st);
+    case 3: return launch_bf16s<BN, 3>(d, tile_prefix, nprob, total_tiles, max_spin, err, st);
+    case 4: return launch_bf16s<BN, 4>(d, tile_prefix, nprob, total_tiles, max_spin, err, st);
+    case 5: return launch_bf16s<BN, 5>(d, tile_prefix, nprob, total_tiles, max_spin, err, st);
+    default: return (int)cudaErrorInvalidValue;
+  }
+}
+}  // namespace
+
 int launch_gemm_bf16s(const OzGemmDesc* d, const long long* tile_prefix, int nprob, long long total_tiles,
-                      long long max_spin, int* err, int bn, void* stream) {
+                      long long max_spin, int* err, int bn, int ns, void* stream) {
   if (total_tiles <= 0) return 0;
   cudaStream_t st = (cudaStream_t)stream;
-  if (bn == 128) {
-    const cudaError_t e =
-        cudaFuncSetAttribute(gemm_bf16s_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM_BYTES);
-    if (e != cudaSuccess) return (int)e;
-    gemm_bf16s_kernel<128><<<(unsigned)total_tiles, OZ_THREADS, OZ_SMEM_BYTES, st>>>(d, tile_prefix, nprob, max_spin, err);
-  } else if (bn == 64) {
-    const cudaError_t e =
-        cudaFuncSetAttribute(gemm_bf16s_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM_BYTES);
-    if (e != cudaSuccess) return (int)e;
-    gemm_bf16s_kernel<64><<<(unsigned)total_tiles, OZ_THREADS, OZ_SMEM_BYTES, st>>>(d, tile_prefix, nprob, max_spin, err);
-  } else {
-    return (int)cudaErrorInvalidValue;
-  }
-  return (int)cudaGetLastError();
+  if (bn == 128) return launch_bf16s_s<128>(d, tile_prefix, nprob, total_tiles, max_spin, err, ns, st);
+  if (bn == 64) return launch_bf16s_s<64>(d, tile_prefix, nprob, total_tiles, max_spin, err, ns, st);
+  return (int)cudaErrorInvalidValue;
 }
 
 }  // namespace tnqe

@@ -162,7 +162,7 @@ __device__ __forceinline__ float pow2f(int e) {
 
 constexpr int OZ_ERR_TIMEOUT = 1;
 
-template <int BN>
+template <int BN, int S>
 __global__ void __launch_bounds__(OZ_THREADS, 1)
     gemm_bf16s_kernel(const OzGemmDesc* __restrict__ descs, const long long* __restrict__ tile_prefix, int nprob,
                       long long max_spin, int* __restrict__ err) {
@@ -190,9 +190,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
   const int m0 = tm * OZ_BM, n0 = tn * BN;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int KT = (d->K + OZ_BK - 1) / OZ_BK;
-  const int S = d->nslices;
-  const int NST = oz_stages(S, BN);
-  const int stage_bytes = oz_stage_bytes(S, BN);
+  constexpr int NST = oz_stages(S, BN);
+  constexpr int stage_bytes = oz_stage_bytes(S, BN);
 
   if (tid == 0) {
     s_fail = 0;
@@ -224,7 +223,6 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     };
     int issued = 0, consumed = 0;
     for (int s = 0; s < NST && s < KT; ++s, ++issued) issue(s, s);
-    bool started3 = false;
     for (int kt = 0; kt < KT && !fail; ++kt) {
       const int s = kt % NST;
       if (!mbar_wait(&full[s], (uint32_t)((kt / NST) & 1), max_spin)) {
@@ -233,22 +231,25 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       }
       consumed = kt + 1;
       tc_fence_after();
-      const uint32_t a0 = smem_u32(stage_a(s)), b0 = smem_u32(stage_b(s));
+      // descriptors differ only in the start-address field (address / 16, 14 bits; the
+      // shared-memory window is below 256 KiB), so offsets are added to one base descriptor
+      const uint64_t da0 = sw64_desc(smem_u32(stage_a(s))), db0 = sw64_desc(smem_u32(stage_b(s)));
 #pragma unroll
       for (int k = 0; k < OZ_BK / 16; ++k) {        // 16 BF16 = 32 bytes per MMA along K
         const uint32_t acc_on = (kt > 0 || k > 0) ? 1u : 0u;
-        auto da = [&](int i) { return sw64_desc(a0 + i * OZ_SLICE_BYTES + 32 * k); };
-        auto db = [&](int j) { return sw64_desc(b0 + j * (BN * OZ_BK * 2) + 32 * k); };
+        auto da = [&](int i) { return da0 + (uint64_t)((i * OZ_SLICE_BYTES + 32 * k) >> 4); };
+        auto db = [&](int j) { return db0 + (uint64_t)((j * (BN * OZ_BK * 2) + 32 * k) >> 4); };
         mma_bf16(tmem + 0 * BN, da(0), db(0), IDESC, acc_on);
         mma_bf16(tmem + 1 * BN, da(0), db(1), IDESC, acc_on);
         mma_bf16(tmem + 2 * BN, da(1), db(0), IDESC, acc_on);
-        // orders 4 .. S + 1 into acc3 (0-based slice indices i + j = 2 .. S - 1)
+        // orders 4 .. S + 1 into acc3 (0-based slice indices i + j = 2 .. S - 1); the first of
+        // them, (0, 2), starts the accumulator
+#pragma unroll
         for (int i = 0; i < S; ++i)
+#pragma unroll
           for (int j = 0; j < S; ++j) {
-            const int ord = i + j;
-            if (ord < 2 || ord > S - 1) continue;
-            mma_bf16(tmem + 3 * BN, da(i), db(j), IDESC, started3 ? 1u : 0u);
-            started3 = true;
+            if (i + j < 2 || i + j > S - 1) continue;
+            mma_bf16(tmem + 3 * BN, da(i), db(j), IDESC, (acc_on || i != 0 || j != 2) ? 1u : 0u);
           }
       }
       mma_commit(&empty[s]);
