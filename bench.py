@@ -267,10 +267,16 @@ def run_native(args):
             "slice_rows/cols/sites_kernel": (prof[10] / K, prof[11] / K, "hbm", peaks["hbm_gbs"], "GB/s"),
         }
     top = max(kern, key=lambda k: kern[k][0])
+    # DRAM bytes per launch from the ncu captures in profiles/ (read + write), scaled from the
+    # captured case to this launch by the units it processes; None where no capture of the
+    # current kernel exists for this workload.
+    n_rot = sum(1 for i, j in pairs if i != j)
+    traffic_table = {("n14_chi128", "rotate_pairs_kernel"): 587.0e6 / 2 * n_rot}   # rotate_pairs_n14_small.md
+    traffic = traffic_table.get((w.name, top))
     t_ms, work, bound, peak, unit = kern[top]
     achieved = (work / (t_ms / 1e3)) / (1e12 if unit == "TFLOP/s" else 1e9) if t_ms > 0 else 0.0
     roof = {"kernel": top, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
-            "frac": achieved / peak if peak else None, "traffic": None,
+            "frac": achieved / peak if peak else None, "traffic": traffic,
             "peak_source": ({"alu": "FP64 = measured bf16 burst x 1.25/2250 (nominal ratio)",
                              "tensor": ("TF32x3 useful = measured bf16 burst x 1.1/2.25 / 3"
                                         if args.precision == "tf32x3" else

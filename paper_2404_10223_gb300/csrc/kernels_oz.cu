@@ -360,14 +360,25 @@ int launch_extract_df(const float2* const* fin, int npairs, double* H, double* S
   return (int)cudaGetLastError();
 }
 namespace {
+int sm_count() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        n <= 0)
+      n = 148;
+  }
+  return n;
+}
 template <int BN, int S>
 int launch_bf16s(const OzGemmDesc* d, const long long* tile_prefix, int nprob, long long total_tiles,
                  long long max_spin, int* err, cudaStream_t st) {
   const cudaError_t e =
       cudaFuncSetAttribute(gemm_bf16s_kernel<BN, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM_BYTES);
   if (e != cudaSuccess) return (int)e;
-  gemm_bf16s_kernel<BN, S><<<(unsigned)total_tiles, OZ_THREADS, OZ_SMEM_BYTES, st>>>(d, tile_prefix, nprob, max_spin,
-                                                                                      err);
+  const long long grid = total_tiles < sm_count() ? total_tiles : sm_count();   // persistent: one CTA per SM
+  gemm_bf16s_kernel<BN, S><<<(unsigned)grid, OZ_THREADS, OZ_SMEM_BYTES, st>>>(d, tile_prefix, nprob, total_tiles,
+                                                                               max_spin, err);
   return (int)cudaGetLastError();
 }
 template <int BN>

@@ -8,6 +8,7 @@
 // are computed, since a Givens gate conserves (n_alpha, n_beta) per spin.
 #include <cuda_runtime.h>
 
+#include "df.cuh"
 #include "internal.h"
 
 namespace tnqe {
@@ -243,11 +244,35 @@ __device__ int block_svd(const double* __restrict__ Bm, double* __restrict__ W, 
       done = !Team::any(rot);
     }
   }
-  // ---- Q = orthogonalised FP32 rotations: Newton-Schulz Q <- Q (1.5 I - 0.5 Q^T Q) in FP64,
-  // twice: the FP32 product is orthogonal to ~1e-6, each step squares the defect
-  for (int idx = tr; idx < n * n; idx += ts) Q[idx] = (double)Q32[idx];
-  Team::sync();
-  for (int it = 0; it < 2; ++it) {
+  // ---- Q = orthogonalised FP32 rotations: Newton-Schulz Q <- Q (1.5 I - 0.5 Q^T Q), each step
+  // squaring the orthogonality defect (about 1e-6 for the FP32 product): the first step in
+  // double-float arithmetic (its result only needs 1e-12), the second in FP64.
+  {
+    float2* Qd = reinterpret_cast<float2*>(T);      // Q as double-float (T holds n x n doubles)
+    float2* Md = reinterpret_cast<float2*>(W);      // 1.5 I - 0.5 Q^T Q (W holds m x n >= n x n doubles)
+    float2* Qn = reinterpret_cast<float2*>(Q);      // the new Q, double-float, converted in place below
+    for (int idx = tr; idx < n * n; idx += ts) Qd[idx] = make_float2(Q32[idx], 0.f);
+    Team::sync();
+    for (int idx = tr; idx < n * n; idx += ts) {
+      const int i = idx % n, j = idx / n;
+      const float2* qi = Qd + (size_t)i * n;
+      const float2* qj = Qd + (size_t)j * n;
+      float2 acc = make_float2(0.f, 0.f);
+      for (int k = 0; k < n; ++k) acc = dfa::fma(qi[k], qj[k], acc);
+      Md[idx] = dfa::add(make_float2(i == j ? 1.5f : 0.f, 0.f), make_float2(-0.5f * acc.x, -0.5f * acc.y));
+    }
+    Team::sync();
+    for (int idx = tr; idx < n * n; idx += ts) {
+      const int row = idx % n, col = idx / n;
+      float2 acc = make_float2(0.f, 0.f);
+      for (int k = 0; k < n; ++k) acc = dfa::fma(Qd[(size_t)k * n + row], Md[(size_t)col * n + k], acc);
+      Qn[idx] = acc;
+    }
+    Team::sync();
+    for (int idx = tr; idx < n * n; idx += ts) Q[idx] = dfa::to_double(Qn[idx]);   // same 8 bytes per element
+    Team::sync();
+  }
+  {
     for (int idx = tr; idx < n * n; idx += ts) {
       const int i = idx % n, j = idx / n;
       const double* qi = Q + (size_t)i * n;
@@ -267,15 +292,30 @@ __device__ int block_svd(const double* __restrict__ Bm, double* __restrict__ W, 
     for (int idx = tr; idx < n * n; idx += ts) Q[idx] = W[idx];
     Team::sync();
   }
-  // ---- W = Bm Q
-  for (int idx = tr; idx < m * n; idx += ts) {
-    const int row = idx % m, col = idx / m;
-    const double* qc = Q + (size_t)col * n;
-    double acc = 0.0;
-    for (int k = 0; k < n; ++k) acc = fma(Bm[(size_t)k * m + row], qc[k], acc);
-    W[idx] = acc;
+  // ---- W = Bm Q in double-float: Bm converted in place (the caller no longer needs it),
+  // Q copied to double-float in T; W comes back to FP64 in place.  Its error (about
+  // 2^-48 relative) is far below the truncation and the FP64 sweeps keep W = Bm Q to it.
+  {
+    float2* Bd = reinterpret_cast<float2*>(const_cast<double*>(Bm));
+    float2* Qd = reinterpret_cast<float2*>(T);
+    float2* Wd = reinterpret_cast<float2*>(W);
+    for (int idx = tr; idx < m * n; idx += ts) {
+      const double b = Bm[idx];
+      Bd[idx] = dfa::from_double(b);
+    }
+    for (int idx = tr; idx < n * n; idx += ts) Qd[idx] = dfa::from_double(Q[idx]);
+    Team::sync();
+    for (int idx = tr; idx < m * n; idx += ts) {
+      const int row = idx % m, col = idx / m;
+      const float2* qc = Qd + (size_t)col * n;
+      float2 acc = make_float2(0.f, 0.f);
+      for (int k = 0; k < n; ++k) acc = dfa::fma(Bd[(size_t)k * m + row], qc[k], acc);
+      Wd[idx] = acc;
+    }
+    Team::sync();
+    for (int idx = tr; idx < m * n; idx += ts) W[idx] = dfa::to_double(Wd[idx]);
+    Team::sync();
   }
-  Team::sync();
   if (n < 2) return noconv;
   // ---- FP64 phase.  A sweep that finds no pair above 1e-7 relative leaves
   // off-diagonals near 1e-14 after its own rotations (quadratic convergence),

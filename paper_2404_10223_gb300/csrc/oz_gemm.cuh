@@ -15,11 +15,13 @@
 // accumulators error-free into a double-float (hi + lo, two FP32 values) and
 // scales by 2^(e_r + e_c).
 //
-// One CTA computes one 128 x BN tile (BN = 128 or 64) of one problem: thread 0
-// issues the TMA loads (3-D boxes: 32 K-elements x rows x S slices, 64-byte
-// swizzle) and the tcgen05.mma instructions; the four accumulators take 4 BN
-// columns of tensor memory; all four warps run the epilogue, staged through
-// shared memory for row-contiguous stores.
+// Persistent: one CTA per SM walks the 128 x BN tiles (BN = 128 or 64) of all
+// problems of the launch.  Thread 0 issues the TMA loads (3-D boxes: 32
+// K-elements x rows x S slices, 64-byte swizzle) and the tcgen05.mma
+// instructions; loads run ahead into the next tile, so its first stages land
+// while the current tile's epilogue runs; the four accumulators take 4 BN
+// columns of tensor memory; all four warps run the epilogue, 16 columns at a
+// time through a small per-warp staging buffer for row-contiguous stores.
 #pragma once
 #include <cuda.h>
 #include <cuda_runtime.h>
@@ -35,8 +37,9 @@ constexpr int OZ_THREADS = 128;
 constexpr int OZ_SLICE_BYTES = OZ_BM * OZ_BK * 2;      // 8 KiB per slice tile
 constexpr int OZ_MAX_STAGES = 4;
 constexpr int OZ_STAGE_AREA = 196608;                  // pipeline stages: 2 S slice tiles each
-constexpr int OZ_GUARD = 16384;                        // slack after the stage area
-constexpr int OZ_SMEM_BYTES = OZ_STAGE_AREA + OZ_GUARD + 1024 /*align*/ + 256 /*barriers*/;
+constexpr int OZ_SLD = 17;                             // staging row stride (float2): 16 columns + 1
+constexpr int OZ_STAGING_BYTES = 4 * 32 * OZ_SLD * 8;  // per-warp epilogue staging, 16 columns at a time
+constexpr int OZ_SMEM_BYTES = OZ_STAGE_AREA + OZ_STAGING_BYTES + 1024 /*align*/ + 256 /*barriers*/;
 // bytes of one pipeline stage: S slice tiles of A (128 rows) and of B (BN rows)
 __host__ __device__ constexpr int oz_stage_bytes(int S, int BN) { return S * (OZ_SLICE_BYTES + BN * OZ_BK * 2); }
 // pipeline depth: as many stages as fit the stage area
@@ -165,11 +168,12 @@ constexpr int OZ_ERR_TIMEOUT = 1;
 template <int BN, int S>
 __global__ void __launch_bounds__(OZ_THREADS, 1)
     gemm_bf16s_kernel(const OzGemmDesc* __restrict__ descs, const long long* __restrict__ tile_prefix, int nprob,
-                      long long max_spin, int* __restrict__ err) {
+                      long long total_tiles, long long max_spin, int* __restrict__ err) {
   using namespace ozdev;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + OZ_STAGE_AREA + OZ_GUARD);
+  float2* staging = reinterpret_cast<float2*>(smem + OZ_STAGE_AREA);          // 4 warps x 32 rows x OZ_SLD
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + OZ_STAGE_AREA + OZ_STAGING_BYTES);
   uint64_t* empty = full + OZ_MAX_STAGES;
   uint64_t* accb = empty + OZ_MAX_STAGES;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accb + 1);
@@ -177,21 +181,29 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
   __shared__ int s_eb[BN];
   constexpr int TMEM_COLS = 4 * BN;                      // four accumulators
   constexpr uint32_t IDESC = oz_idesc<BN>();
-
-  const long long tile = blockIdx.x;
-  int lo = 0, hi = nprob - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (tile_prefix[mid] <= tile) lo = mid; else hi = mid - 1;
-  }
-  const OzGemmDesc* d = descs + lo;
-  const long long local = tile - tile_prefix[lo];
-  const int tm = (int)(local / d->tiles_n), tn = (int)(local % d->tiles_n);
-  const int m0 = tm * OZ_BM, n0 = tn * BN;
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int KT = (d->K + OZ_BK - 1) / OZ_BK;
   constexpr int NST = oz_stages(S, BN);
   constexpr int stage_bytes = oz_stage_bytes(S, BN);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+  struct Tile {
+    const OzGemmDesc* d;
+    int m0, n0, KT;
+  };
+  auto tile_of = [&](long long t) -> Tile {
+    Tile r{nullptr, 0, 0, 0};
+    if (t >= total_tiles) return r;
+    int lo = 0, hi = nprob - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (tile_prefix[mid] <= t) lo = mid; else hi = mid - 1;
+    }
+    r.d = descs + lo;
+    const long long local = t - tile_prefix[lo];
+    r.m0 = (int)(local / r.d->tiles_n) * OZ_BM;
+    r.n0 = (int)(local % r.d->tiles_n) * BN;
+    r.KT = (r.d->K + OZ_BK - 1) / OZ_BK;
+    return r;
+  };
 
   if (tid == 0) {
     s_fail = 0;
@@ -211,114 +223,140 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
+  // Producer / MMA state (thread 0).  Loads and consumptions are numbered over all
+  // k-tiles this CTA handles; load g goes to stage g % NST.  Loads run ahead into the
+  // next tile, so its first stages land while the current tile's epilogue runs.
+  long long base = 0;          // global index of the current tile's first k-tile
+  long long issued = 0;        // loads issued so far
+  Tile cur = tile_of(blockIdx.x), nxt = tile_of(blockIdx.x + (long long)gridDim.x);
   int fail = 0;
-  if (tid == 0) {
-    const uint32_t tx = (uint32_t)stage_bytes;
-    auto stage_a = [&](int s) { return smem + s * stage_bytes; };
-    auto stage_b = [&](int s) { return smem + s * stage_bytes + S * OZ_SLICE_BYTES; };
-    auto issue = [&](int s, int kt) {
-      mbar_expect_tx(&full[s], tx);
-      tma_load_3d(stage_a(s), &d->mapA, &full[s], kt * OZ_BK, m0, 0);
-      tma_load_3d(stage_b(s), &d->mapB, &full[s], kt * OZ_BK, n0, 0);
-    };
-    int issued = 0, consumed = 0;
-    for (int s = 0; s < NST && s < KT; ++s, ++issued) issue(s, s);
-    for (int kt = 0; kt < KT && !fail; ++kt) {
-      const int s = kt % NST;
-      if (!mbar_wait(&full[s], (uint32_t)((kt / NST) & 1), max_spin)) {
+  auto stage_a = [&](int s) { return smem + s * stage_bytes; };
+  auto stage_b = [&](int s) { return smem + s * stage_bytes + S * OZ_SLICE_BYTES; };
+  // issue loads while issued < limit and the load exists in the current or next tile
+  auto issue_upto = [&](long long limit) {
+    while (!fail && issued < limit) {
+      const Tile* t;
+      int kt;
+      if (issued < base + cur.KT) {
+        t = &cur;
+        kt = (int)(issued - base);
+      } else if (nxt.d && issued < base + cur.KT + nxt.KT) {
+        t = &nxt;
+        kt = (int)(issued - base - cur.KT);
+      } else {
+        return;
+      }
+      const int s = (int)(issued % NST);
+      if (issued >= NST && !mbar_wait(&empty[s], (uint32_t)(((issued - NST) / NST) & 1), max_spin)) {
         fail = 1;
-        break;
+        return;
       }
-      consumed = kt + 1;
-      tc_fence_after();
-      // descriptors differ only in the start-address field (address / 16, 14 bits; the
-      // shared-memory window is below 256 KiB), so offsets are added to one base descriptor
-      const uint64_t da0 = sw64_desc(smem_u32(stage_a(s))), db0 = sw64_desc(smem_u32(stage_b(s)));
-#pragma unroll
-      for (int k = 0; k < OZ_BK / 16; ++k) {        // 16 BF16 = 32 bytes per MMA along K
-        const uint32_t acc_on = (kt > 0 || k > 0) ? 1u : 0u;
-        auto da = [&](int i) { return da0 + (uint64_t)((i * OZ_SLICE_BYTES + 32 * k) >> 4); };
-        auto db = [&](int j) { return db0 + (uint64_t)((j * (BN * OZ_BK * 2) + 32 * k) >> 4); };
-        mma_bf16(tmem + 0 * BN, da(0), db(0), IDESC, acc_on);
-        mma_bf16(tmem + 1 * BN, da(0), db(1), IDESC, acc_on);
-        mma_bf16(tmem + 2 * BN, da(1), db(0), IDESC, acc_on);
-        // orders 4 .. S + 1 into acc3 (0-based slice indices i + j = 2 .. S - 1); the first of
-        // them, (0, 2), starts the accumulator
-#pragma unroll
-        for (int i = 0; i < S; ++i)
-#pragma unroll
-          for (int j = 0; j < S; ++j) {
-            if (i + j < 2 || i + j > S - 1) continue;
-            mma_bf16(tmem + 3 * BN, da(i), db(j), IDESC, (acc_on || i != 0 || j != 2) ? 1u : 0u);
-          }
-      }
-      mma_commit(&empty[s]);
-      // refill the stage read by the previous k-tile once its MMAs are done
-      if (kt >= 1 && kt - 1 + NST < KT) {
-        const int sp = (kt - 1) % NST;
-        if (!mbar_wait(&empty[sp], (uint32_t)(((kt - 1) / NST) & 1), max_spin)) {
+      mbar_expect_tx(&full[s], (uint32_t)stage_bytes);
+      tma_load_3d(stage_a(s), &t->d->mapA, &full[s], kt * OZ_BK, t->m0, 0);
+      tma_load_3d(stage_b(s), &t->d->mapB, &full[s], kt * OZ_BK, t->n0, 0);
+      ++issued;
+    }
+  };
+  if (tid == 0) issue_upto(NST);
+
+  long long ntile = 0;
+  for (long long tile = blockIdx.x; tile < total_tiles; tile += gridDim.x, ++ntile) {
+    const Tile me = tile_of(tile);                      // every thread: this tile's problem and origin
+    // ---- mainloop (thread 0); the other warps fetch the column exponents meanwhile
+    if (tid == 0 && !fail) {
+      for (int kt = 0; kt < cur.KT; ++kt) {
+        const long long c = base + kt;
+        const int s = (int)(c % NST);
+        if (!mbar_wait(&full[s], (uint32_t)((c / NST) & 1), max_spin)) {
           fail = 1;
           break;
         }
-        issue(sp, kt - 1 + NST);
-        ++issued;
-      }
-    }
-    mma_commit(accb);   // arrives once every issued MMA is done, also after a failure
-    if (fail)           // let the loads still in flight land before the CTA leaves
-      for (int q = consumed; q < issued; ++q) mbar_wait(&full[q % NST], (uint32_t)((q / NST) & 1), max_spin);
-  }
-  if (tid < BN) s_eb[tid] = n0 + tid < d->N ? d->eb[n0 + tid] : 0;
-  if (!mbar_wait(accb, 0, max_spin)) fail = 1;
-  tc_fence_after();
-  if (fail) {
-    s_fail = 1;
-    atomicExch(err, OZ_ERR_TIMEOUT);
-  }
-  __syncthreads();
-  if (!s_fail) {
-    // The stage area is free once every MMA has completed: stage the tile there
-    // as (hi, lo) rows (padded by one element against bank conflicts), then each
-    // warp stores its 32 rows with consecutive lanes on consecutive columns.
-    float2* stg = reinterpret_cast<float2*>(smem);
-    constexpr int SLD = BN + 1;
-    const int row = m0 + warp * 32 + lane;
-    const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
-    const bool has3 = S >= 3;
-    const int era = row < d->M ? d->ea[row] : 0;
-    float2* srow = stg + (warp * 32 + lane) * SLD;
-#pragma unroll 1
-    for (int c0 = 0; c0 < BN; c0 += 16) {
-      uint32_t v0[16], v1[16], v2[16], v3[16];
-      tmem_ld16(lane_base + 0 * BN + c0, v0);
-      tmem_ld16(lane_base + 1 * BN + c0, v1);
-      tmem_ld16(lane_base + 2 * BN + c0, v2);
-      tmem_ld16(lane_base + 3 * BN + c0, v3);
-      tmem_wait_ld();
+        tc_fence_after();
+        const uint64_t da0 = sw64_desc(smem_u32(stage_a(s))), db0 = sw64_desc(smem_u32(stage_b(s)));
 #pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        float s, e, e2;
-        two_sum(__uint_as_float(v0[j]), __uint_as_float(v1[j]), s, e);
-        two_sum(s, __uint_as_float(v2[j]), s, e2);
-        e += e2;
-        if (has3) e += __uint_as_float(v3[j]);
-        const float h = s + e;
-        const float l = e - (h - s);
-        const int ex = era + s_eb[c0 + j];
-        const float s1 = pow2f(ex / 2), s2 = pow2f(ex - ex / 2);
-        srow[c0 + j] = make_float2(h * s1 * s2, l * s1 * s2);
+        for (int k = 0; k < OZ_BK / 16; ++k) {        // 16 BF16 = 32 bytes per MMA along K
+          const uint32_t acc_on = (kt > 0 || k > 0) ? 1u : 0u;
+          auto da = [&](int i) { return da0 + (uint64_t)((i * OZ_SLICE_BYTES + 32 * k) >> 4); };
+          auto db = [&](int j) { return db0 + (uint64_t)((j * (BN * OZ_BK * 2) + 32 * k) >> 4); };
+          mma_bf16(tmem + 0 * BN, da(0), db(0), IDESC, acc_on);
+          mma_bf16(tmem + 1 * BN, da(0), db(1), IDESC, acc_on);
+          mma_bf16(tmem + 2 * BN, da(1), db(0), IDESC, acc_on);
+#pragma unroll
+          for (int i = 0; i < S; ++i)
+#pragma unroll
+            for (int j = 0; j < S; ++j) {
+              if (i + j < 2 || i + j > S - 1) continue;
+              mma_bf16(tmem + 3 * BN, da(i), db(j), IDESC, (acc_on || i != 0 || j != 2) ? 1u : 0u);
+            }
+        }
+        mma_commit(&empty[s]);
+        if (kt >= 1) issue_upto(c - 1 + NST + 1);       // refill the stage of k-tile c - 1
+      }
+      mma_commit(accb);                                 // arrives once every issued MMA is done
+    }
+    if (warp != 0)
+      for (int i = tid - 32; i < BN; i += OZ_THREADS - 32) s_eb[i] = me.n0 + i < me.d->N ? me.d->eb[me.n0 + i] : 0;
+    const int row = me.m0 + warp * 32 + lane;
+    const int era = row < me.d->M ? me.d->ea[row] : 0;
+    if (!mbar_wait(accb, (uint32_t)(ntile & 1), max_spin)) fail = 1;
+    tc_fence_after();
+    if (tid == 0 && !fail) issue_upto(base + cur.KT + NST);   // every stage is free: fill them for the next tile
+    if (fail) atomicExch(&s_fail, 1);
+    __syncthreads();
+    if (s_fail) break;
+    // ---- epilogue: TMEM -> (hi, lo) -> per-warp staging -> rows of C
+    {
+      const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+      float2* stg = staging + warp * 32 * OZ_SLD;
+      const int ncols = min(BN, me.d->N - me.n0);
+      const int mrows = me.d->M;
+      const long long ldc = me.d->ldc;
+      float2* Ct = me.d->C + me.n0;
+#pragma unroll 1
+      for (int c0 = 0; c0 < BN; c0 += 16) {
+        uint32_t v0[16], v1[16], v2[16], v3[16];
+        tmem_ld16(lane_base + 0 * BN + c0, v0);
+        tmem_ld16(lane_base + 1 * BN + c0, v1);
+        tmem_ld16(lane_base + 2 * BN + c0, v2);
+        tmem_ld16(lane_base + 3 * BN + c0, v3);
+        tmem_wait_ld();
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          float s, e, e2;
+          two_sum(__uint_as_float(v0[j]), __uint_as_float(v1[j]), s, e);
+          two_sum(s, __uint_as_float(v2[j]), s, e2);
+          e += e2;
+          if (S >= 3) e += __uint_as_float(v3[j]);
+          const float h = s + e;
+          const float l = e - (h - s);
+          const int ex = era + s_eb[c0 + j];
+          const float s1 = pow2f(ex / 2), s2 = pow2f(ex - ex / 2);
+          stg[lane * OZ_SLD + j] = make_float2(h * s1 * s2, l * s1 * s2);
+        }
+        __syncwarp();
+        const int col = c0 + (lane & 15);
+#pragma unroll 4
+        for (int rr = 0; rr < 32; rr += 2) {
+          const int r = rr + (lane >> 4);
+          const int grow = me.m0 + warp * 32 + r;
+          if (grow < mrows && col < ncols) Ct[(long long)grow * ldc + col] = stg[r * OZ_SLD + (lane & 15)];
+        }
+        __syncwarp();
       }
     }
-    __syncwarp();
-    const int ncols = min(BN, d->N - n0);
-#pragma unroll 1
-    for (int rr = 0; rr < 32; ++rr) {
-      const int grow = m0 + warp * 32 + rr;
-      if (grow >= d->M) break;
-      float2* crow = d->C + (long long)grow * d->ldc + n0;
-      const float2* sr = stg + (warp * 32 + rr) * SLD;
-      for (int cc = lane; cc < ncols; cc += 32) crow[cc] = sr[cc];
+    tc_fence_before();
+    __syncthreads();                                    // TMEM read out before the next tile's MMAs
+    tc_fence_after();
+    if (tid == 0) {
+      base += cur.KT;
+      cur = nxt;
+      nxt = tile_of(tile + 2LL * gridDim.x);
     }
+  }
+  if (tid == 0 && (fail || s_fail)) {
+    atomicExch(err, OZ_ERR_TIMEOUT);
+    // let the loads still in flight land before the CTA leaves
+    for (long long q = base; q < issued; ++q) mbar_wait(&full[q % NST], (uint32_t)((q / NST) & 1), max_spin);
   }
   tc_fence_before();
   __syncthreads();
