@@ -192,6 +192,9 @@ def run_native(args):
     tnqe.load()
     w = inputs.workload(args.workload)
     pairs = w.all_pairs()
+    if args.states:                       # only the pairs among these states (profiling captures)
+        keep = {int(x) for x in args.states.split(",")}
+        pairs = [(i, j) for i, j in pairs if i in keep and j in keep]
     if args.max_pairs > 0:                # a smaller case of the same workload (profiling captures)
         pairs = pairs[:args.max_pairs]
     npairs = len(pairs)
@@ -373,6 +376,7 @@ def main():
     ap.add_argument("--max-pairs", type=int, default=0, help="use only the first K pairs (profiling on a small case)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-buffer leg")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes (profiling)")
+    ap.add_argument("--states", default="", help="comma-separated state ids: only pairs among them (profiling)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
