@@ -204,7 +204,10 @@ def run_native(args):
     for m in w.mps:
         g.add_mps(m.tensors, m.U)
     tuned = None
-    if args.precision.startswith("bf16") and not args.no_autotune:
+    if args.shapes:
+        tuned = [int(x) for x in args.shapes.split(",")]
+        g.set_tuning(*tuned)
+    elif args.precision.startswith("bf16") and not args.no_autotune:
         tuned, _ = g.autotune(pairs)      # launch shapes, chosen outside the timed region
     Hd = torch.zeros(npairs, dtype=torch.float64, device="cuda")
     Sd = torch.zeros(npairs, dtype=torch.float64, device="cuda")
@@ -376,6 +379,7 @@ def main():
     ap.add_argument("--max-pairs", type=int, default=0, help="use only the first K pairs (profiling on a small case)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-buffer leg")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes (profiling)")
+    ap.add_argument("--shapes", default="", help="bn1,bn3,spmm_bw launch shapes instead of autotuning")
     ap.add_argument("--states", default="", help="comma-separated state ids: only pairs among them (profiling)")
     args = ap.parse_args()
     if args.impl == "reference":

@@ -381,6 +381,17 @@ int launch_bf16s(const OzGemmDesc* d, const long long* tile_prefix, int nprob, l
                                                                                max_spin, err);
   return (int)cudaGetLastError();
 }
+template <int S>
+int launch_bf16s_ws(const OzGemmDesc* d, const long long* tile_prefix, int nprob, long long total_tiles,
+                    long long max_spin, int* err, cudaStream_t st) {
+  const cudaError_t e =
+      cudaFuncSetAttribute(gemm_bf16s_ws_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM_BYTES);
+  if (e != cudaSuccess) return (int)e;
+  const long long grid = total_tiles < sm_count() ? total_tiles : sm_count();
+  gemm_bf16s_ws_kernel<S><<<(unsigned)grid, OZW_THREADS, OZ_SMEM_BYTES, st>>>(d, tile_prefix, nprob, total_tiles,
+                                                                               max_spin, err);
+  return (int)cudaGetLastError();
+}
 template <int BN>
 int launch_bf16s_s(const OzGemmDesc* d, const long long* tile_prefix, int nprob, long long total_tiles,
                    long long max_spin, int* err, int ns, cudaStream_t st) {
@@ -399,7 +410,15 @@ int launch_gemm_bf16s(const OzGemmDesc* d, const long long* tile_prefix, int npr
   if (total_tiles <= 0) return 0;
   cudaStream_t st = (cudaStream_t)stream;
   if (bn == 128) return launch_bf16s_s<128>(d, tile_prefix, nprob, total_tiles, max_spin, err, ns, st);
-  if (bn == 64) return launch_bf16s_s<64>(d, tile_prefix, nprob, total_tiles, max_spin, err, ns, st);
+  if (bn == 64) {                                   // warp-specialised, double-buffered accumulators
+    switch (ns) {
+      case 2: return launch_bf16s_ws<2>(d, tile_prefix, nprob, total_tiles, max_spin, err, st);
+      case 3: return launch_bf16s_ws<3>(d, tile_prefix, nprob, total_tiles, max_spin, err, st);
+      case 4: return launch_bf16s_ws<4>(d, tile_prefix, nprob, total_tiles, max_spin, err, st);
+      case 5: return launch_bf16s_ws<5>(d, tile_prefix, nprob, total_tiles, max_spin, err, st);
+      default: return (int)cudaErrorInvalidValue;
+    }
+  }
   return (int)cudaErrorInvalidValue;
 }
 

@@ -365,6 +365,234 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     tmem_dealloc(tmem, TMEM_COLS);
   }
 }
+
+// Warp-specialised variant with N = 64 tiles and two TMEM accumulator sets
+// (2 x 4 x 64 = 512 columns): warp 4 (one lane) issues the TMA loads and the
+// MMAs of tile t into set t % 2 while warps 0-3 read tile t - 1 out of the
+// other set, so the tensor pipe keeps working through the epilogue.
+constexpr int OZW_THREADS = 160;
+namespace ozdev {
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+}  // namespace ozdev
+
+template <int S>
+__global__ void __launch_bounds__(OZW_THREADS, 1)
+    gemm_bf16s_ws_kernel(const OzGemmDesc* __restrict__ descs, const long long* __restrict__ tile_prefix, int nprob,
+                         long long total_tiles, long long max_spin, int* __restrict__ err) {
+  using namespace ozdev;
+  constexpr int BN = 64;
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  float2* staging = reinterpret_cast<float2*>(smem + OZ_STAGE_AREA);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + OZ_STAGE_AREA + OZ_STAGING_BYTES);
+  uint64_t* empty = full + OZ_MAX_STAGES;
+  uint64_t* accb = empty + OZ_MAX_STAGES;           // [2]: accumulator set ready
+  uint64_t* tempty = accb + 2;                      // [2]: accumulator set read out (4 warp arrivals)
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + 2);
+  __shared__ volatile int s_fail;
+  __shared__ int s_eb[4][BN];                       // per epilogue warp
+  constexpr int TMEM_COLS = 512;
+  constexpr uint32_t IDESC = oz_idesc<BN>();
+  constexpr int NST = oz_stages(S, BN);
+  constexpr int stage_bytes = oz_stage_bytes(S, BN);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+  struct Tile {
+    const OzGemmDesc* d;
+    int m0, n0, KT;
+  };
+  auto tile_of = [&](long long t) -> Tile {
+    Tile r{nullptr, 0, 0, 0};
+    if (t >= total_tiles) return r;
+    int lo = 0, hi = nprob - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (tile_prefix[mid] <= t) lo = mid; else hi = mid - 1;
+    }
+    r.d = descs + lo;
+    const long long local = t - tile_prefix[lo];
+    r.m0 = (int)(local / r.d->tiles_n) * OZ_BM;
+    r.n0 = (int)(local % r.d->tiles_n) * BN;
+    r.KT = (r.d->K + OZ_BK - 1) / OZ_BK;
+    return r;
+  };
+
+  if (tid == 0) {
+    s_fail = 0;
+    for (int s = 0; s < OZ_MAX_STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&accb[b], 1);
+      mbar_init(&tempty[b], 4);
+    }
+    fence_mbar_init();
+  }
+  if (warp == 0) {
+    tmem_alloc(tmem_slot, TMEM_COLS);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 4) {
+    if (lane == 0) {
+      // ---- producer and MMA issuer
+      long long base = 0, issued = 0;
+      Tile cur = tile_of(blockIdx.x), nxt = tile_of(blockIdx.x + (long long)gridDim.x);
+      int fail = 0;
+      auto stage_a = [&](int s) { return smem + s * stage_bytes; };
+      auto stage_b = [&](int s) { return smem + s * stage_bytes + S * OZ_SLICE_BYTES; };
+      auto issue_upto = [&](long long limit) {
+        while (!fail && issued < limit) {
+          const Tile* t;
+          int kt;
+          if (issued < base + cur.KT) {
+            t = &cur;
+            kt = (int)(issued - base);
+          } else if (nxt.d && issued < base + cur.KT + nxt.KT) {
+            t = &nxt;
+            kt = (int)(issued - base - cur.KT);
+          } else {
+            return;
+          }
+          const int s = (int)(issued % NST);
+          if (issued >= NST && !mbar_wait(&empty[s], (uint32_t)(((issued - NST) / NST) & 1), max_spin)) {
+            fail = 1;
+            return;
+          }
+          mbar_expect_tx(&full[s], (uint32_t)stage_bytes);
+          tma_load_3d(stage_a(s), &t->d->mapA, &full[s], kt * OZ_BK, t->m0, 0);
+          tma_load_3d(stage_b(s), &t->d->mapB, &full[s], kt * OZ_BK, t->n0, 0);
+          ++issued;
+        }
+      };
+      issue_upto(NST);
+      long long lt = 0;
+      for (long long tile = blockIdx.x; tile < total_tiles && !fail && !s_fail; tile += gridDim.x, ++lt) {
+        const int b = (int)(lt & 1);
+        if (lt >= 2 && !mbar_wait(&tempty[b], (uint32_t)(((lt - 2) >> 1) & 1), max_spin)) {
+          fail = 1;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t tacc = tmem + (uint32_t)(b * 4 * BN);
+        for (int kt = 0; kt < cur.KT; ++kt) {
+          const long long c = base + kt;
+          const int s = (int)(c % NST);
+          if (!mbar_wait(&full[s], (uint32_t)((c / NST) & 1), max_spin)) {
+            fail = 1;
+            break;
+          }
+          tc_fence_after();
+          const uint64_t da0 = sw64_desc(smem_u32(stage_a(s))), db0 = sw64_desc(smem_u32(stage_b(s)));
+#pragma unroll
+          for (int k = 0; k < OZ_BK / 16; ++k) {
+            const uint32_t acc_on = (kt > 0 || k > 0) ? 1u : 0u;
+            auto da = [&](int i) { return da0 + (uint64_t)((i * OZ_SLICE_BYTES + 32 * k) >> 4); };
+            auto db = [&](int j) { return db0 + (uint64_t)((j * (BN * OZ_BK * 2) + 32 * k) >> 4); };
+            mma_bf16(tacc + 0 * BN, da(0), db(0), IDESC, acc_on);
+            mma_bf16(tacc + 1 * BN, da(0), db(1), IDESC, acc_on);
+            mma_bf16(tacc + 2 * BN, da(1), db(0), IDESC, acc_on);
+#pragma unroll
+            for (int i = 0; i < S; ++i)
+#pragma unroll
+              for (int j = 0; j < S; ++j) {
+                if (i + j < 2 || i + j > S - 1) continue;
+                mma_bf16(tacc + 3 * BN, da(i), db(j), IDESC, (acc_on || i != 0 || j != 2) ? 1u : 0u);
+              }
+          }
+          mma_commit(&empty[s]);
+          if (kt >= 1) issue_upto(c - 1 + NST + 1);
+        }
+        mma_commit(&accb[b]);                            // arrives once every issued MMA is done
+        if (fail) break;
+        issue_upto(base + cur.KT + NST - 1);             // loads that only needed earlier k-tiles
+        base += cur.KT;
+        cur = nxt;
+        nxt = tile_of(tile + 2LL * gridDim.x);
+      }
+      if (fail) {
+        s_fail = 1;
+        atomicExch(err, OZ_ERR_TIMEOUT);
+      }
+      // let the loads still in flight land before the CTA leaves
+      for (long long q = base; q < issued; ++q) mbar_wait(&full[q % NST], (uint32_t)((q / NST) & 1), max_spin);
+    }
+  } else {
+    // ---- epilogue warps 0-3: TMEM set t % 2 -> (hi, lo) -> per-warp staging -> rows of C
+    long long lt = 0;
+    for (long long tile = blockIdx.x; tile < total_tiles; tile += gridDim.x, ++lt) {
+      if (s_fail) break;
+      const Tile me = tile_of(tile);
+      const int b = (int)(lt & 1);
+      for (int i = lane; i < BN; i += 32) s_eb[warp][i] = me.n0 + i < me.d->N ? me.d->eb[me.n0 + i] : 0;
+      const int row = me.m0 + warp * 32 + lane;
+      const int era = row < me.d->M ? me.d->ea[row] : 0;
+      __syncwarp();
+      if (!mbar_wait(&accb[b], (uint32_t)((lt >> 1) & 1), max_spin)) {
+        s_fail = 1;
+        atomicExch(err, OZ_ERR_TIMEOUT);
+        break;
+      }
+      tc_fence_after();
+      const uint32_t lane_base = tmem + (uint32_t)(b * 4 * BN) + ((uint32_t)(warp * 32) << 16);
+      float2* stg = staging + warp * 32 * OZ_SLD;
+      const int ncols = min(BN, me.d->N - me.n0);
+      const int mrows = me.d->M;
+      const long long ldc = me.d->ldc;
+      float2* Ct = me.d->C + me.n0;
+#pragma unroll 1
+      for (int c0 = 0; c0 < BN; c0 += 16) {
+        uint32_t v0[16], v1[16], v2[16], v3[16];
+        tmem_ld16(lane_base + 0 * BN + c0, v0);
+        tmem_ld16(lane_base + 1 * BN + c0, v1);
+        tmem_ld16(lane_base + 2 * BN + c0, v2);
+        tmem_ld16(lane_base + 3 * BN + c0, v3);
+        tmem_wait_ld();
+        if (c0 + 16 >= BN) {                             // this warp's lanes are read out: free the set
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&tempty[b]);
+        }
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          float s, e, e2;
+          two_sum(__uint_as_float(v0[j]), __uint_as_float(v1[j]), s, e);
+          two_sum(s, __uint_as_float(v2[j]), s, e2);
+          e += e2;
+          if (S >= 3) e += __uint_as_float(v3[j]);
+          const float h = s + e;
+          const float l = e - (h - s);
+          const int ex = era + s_eb[warp][c0 + j];
+          const float s1 = pow2f(ex / 2), s2 = pow2f(ex - ex / 2);
+          stg[lane * OZ_SLD + j] = make_float2(h * s1 * s2, l * s1 * s2);
+        }
+        __syncwarp();
+        const int col = c0 + (lane & 15);
+#pragma unroll 4
+        for (int rr = 0; rr < 32; rr += 2) {
+          const int r = rr + (lane >> 4);
+          const int grow = me.m0 + warp * 32 + r;
+          if (grow < mrows && col < ncols) Ct[(long long)grow * ldc + col] = stg[r * OZ_SLD + (lane & 15)];
+        }
+        __syncwarp();
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    tmem_dealloc(tmem, TMEM_COLS);
+  }
+}
+
 #endif
 
 }  // namespace tnqe
