@@ -145,37 +145,49 @@ __device__ __forceinline__ double exp2_neg_exponent(double x) {
   return __hiloint2double((1023 - ex) << 20, 0);
 }
 
-// A team of threads that works on one SVD block: a single warp, or the whole CTA.
+// A team of threads that works on one SVD block: a single warp, or a group of
+// whole warps with its own named barrier (barrier 0 belongs to __syncthreads).
 struct WarpTeam {
-  __device__ static int rank() { return threadIdx.x & 31; }
-  __device__ static int size() { return 32; }
-  __device__ static void sync() { __syncwarp(); }
-  __device__ static int any(int v) { return __any_sync(0xffffffffu, v); }
-  __device__ static float max(float v, float* /*scratch*/) {
+  __device__ int rank() const { return threadIdx.x & 31; }
+  __device__ int size() const { return 32; }
+  __device__ void sync() const { __syncwarp(); }
+  __device__ int any(int v) const { return __any_sync(0xffffffffu, v); }
+  __device__ float max(float v) const {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
     return v;
   }
 };
-struct CtaTeam {
-  __device__ static int rank() { return threadIdx.x; }
-  __device__ static int size() { return RT_THREADS; }
-  __device__ static void sync() { __syncthreads(); }
-  __device__ static int any(int v) { return __syncthreads_or(v); }
-  __device__ static float max(float v, float* scratch) {   // v >= 0
+struct SubTeam {
+  int base, nthr, bar;             // first thread, thread count (multiple of 32), barrier id
+  float* scratch;                  // one float of shared memory owned by the team
+  __device__ int rank() const { return (int)threadIdx.x - base; }
+  __device__ int size() const { return nthr; }
+  __device__ void sync() const { asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(nthr) : "memory"); }
+  __device__ int any(int v) const {
+    int r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\tsetp.ne.s32 p, %1, 0;\n\tbar.red.or.pred q, %2, %3, p;\n\t"
+        "selp.s32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"(v), "r"(bar), "r"(nthr)
+        : "memory");
+    return r;
+  }
+  __device__ float max(float v) const {   // v >= 0
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
-    if (threadIdx.x == 0) *scratch = 0.f;
-    __syncthreads();
+    if (rank() == 0) *scratch = 0.f;
+    sync();
     if ((threadIdx.x & 31) == 0) atomicMax(reinterpret_cast<int*>(scratch), __float_as_int(v));
-    __syncthreads();
+    sync();
     const float r = *scratch;
-    __syncthreads();
+    sync();
     return r;
   }
 };
 
-// SVD of one block by a team (one warp, or the CTA for large blocks), mixed precision.
+// SVD of one block by a team (one warp, or a group of warps), mixed precision.
 // Bm (m x n column-major, n <= m, scaled to max |entry| = 1) is left untouched;
 // on return W = Bm Q with mutually orthogonal columns (FP64) and Q (n x n)
 // orthogonal to FP64 precision.  Steps: FP32 one-sided Jacobi on a copy of Bm
@@ -185,11 +197,18 @@ struct CtaTeam {
 // computed in FP32, cos/sin normalised in FP64 so every rotation is orthogonal
 // in FP64).  Column pairs of a tournament round go to the team's 8-lane groups.
 // Returns 1 if a phase hit the sweep limit.
+//
+// GB300 executes FP64 at 1/64 of its FP32 rate, so the FP64 sweeps take one
+// dot product per column pair (gamma = x.y): the squared column norms are
+// computed once and carried through every rotation by the exact 2 x 2 Gram
+// update (summed again from the column where that update cancels, so each
+// carried norm keeps a relative error of a few m eps per rotation), and a
+// rotation whose cosine rounds to 1 costs one FMA per element.
 template <class Team>
-__device__ int block_svd(const double* __restrict__ Bm, double* __restrict__ W, double* __restrict__ Q,
-                         float* __restrict__ W32, float* __restrict__ Q32, double* __restrict__ T, int m, int n,
-                         int max_sweeps, float* fscratch) {
-  const int tr = Team::rank(), ts = Team::size();
+__device__ int block_svd(const Team& tm, const double* __restrict__ Bm, double* __restrict__ W,
+                         double* __restrict__ Q, float* __restrict__ W32, float* __restrict__ Q32,
+                         double* __restrict__ T, int m, int n, int max_sweeps) {
+  const int tr = tm.rank(), ts = tm.size();
   const int lane = threadIdx.x & 31, grp = tr >> 3, ngrp = ts >> 3, gl = tr & 7;
   const unsigned gmask = 0xffu << ((lane >> 3) * 8);
   const int n2 = n + (n & 1);
@@ -197,12 +216,13 @@ __device__ int block_svd(const double* __restrict__ Bm, double* __restrict__ W, 
   // ---- FP32 phase
   for (int idx = tr; idx < m * n; idx += ts) W32[idx] = (float)Bm[idx];
   for (int idx = tr; idx < n * n; idx += ts) Q32[idx] = (idx / n == idx % n) ? 1.f : 0.f;
-  Team::sync();
+  tm.sync();
   if (n >= 2) {
     const float tol32 = 1.2e-7f * (float)m;
     int done = 0;
     for (int sweep = 0; sweep < max_sweeps && !done; ++sweep) {
       int rot = 0;
+      float worst = 0.f;                           // largest gamma^2 / (alpha beta) of the sweep
       for (int r = 0; r < n2 - 1; ++r) {
         for (int k = grp; k < n2 / 2; k += ngrp) {
           int i, j;
@@ -221,6 +241,7 @@ __device__ int block_svd(const double* __restrict__ Bm, double* __restrict__ W, 
           be = grp8_sum(be, gmask);
           ga = grp8_sum(ga, gmask);
           if (ga == 0.f || al < 1e-30f || be < 1e-30f || !(fabsf(ga) > tol32 * sqrtf(al) * sqrtf(be))) continue;
+          worst = fmaxf(worst, (ga / al) * (ga / be));
           const float zeta = (be - al) / (2.f * ga);
           const float t = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + hypotf(1.f, zeta));
           const float c = rsqrtf(1.f + t * t), s = c * t;
@@ -239,9 +260,12 @@ __device__ int block_svd(const double* __restrict__ Bm, double* __restrict__ W, 
           }
           rot = 1;
         }
-        Team::sync();
+        tm.sync();
       }
-      done = !Team::any(rot);
+      // A sweep whose largest relative off-diagonal was below 1e-4 leaves the
+      // columns orthogonal to the FP32 floor (quadratic convergence): the
+      // confirming sweep is skipped.  The FP64 phase needs no more than that.
+      done = !tm.any(rot) || tm.max(worst) <= 1e-8f;
     }
   }
   // ---- Q = orthogonalised FP32 rotations: Newton-Schulz Q <- Q (1.5 I - 0.5 Q^T Q), each step
@@ -252,7 +276,7 @@ __device__ int block_svd(const double* __restrict__ Bm, double* __restrict__ W, 
     float2* Md = reinterpret_cast<float2*>(W);      // 1.5 I - 0.5 Q^T Q (W holds m x n >= n x n doubles)
     float2* Qn = reinterpret_cast<float2*>(Q);      // the new Q, double-float, converted in place below
     for (int idx = tr; idx < n * n; idx += ts) Qd[idx] = make_float2(Q32[idx], 0.f);
-    Team::sync();
+    tm.sync();
     for (int idx = tr; idx < n * n; idx += ts) {
       const int i = idx % n, j = idx / n;
       const float2* qi = Qd + (size_t)i * n;
@@ -261,36 +285,44 @@ __device__ int block_svd(const double* __restrict__ Bm, double* __restrict__ W, 
       for (int k = 0; k < n; ++k) acc = dfa::fma(qi[k], qj[k], acc);
       Md[idx] = dfa::add(make_float2(i == j ? 1.5f : 0.f, 0.f), make_float2(-0.5f * acc.x, -0.5f * acc.y));
     }
-    Team::sync();
+    tm.sync();
     for (int idx = tr; idx < n * n; idx += ts) {
       const int row = idx % n, col = idx / n;
       float2 acc = make_float2(0.f, 0.f);
       for (int k = 0; k < n; ++k) acc = dfa::fma(Qd[(size_t)k * n + row], Md[(size_t)col * n + k], acc);
       Qn[idx] = acc;
     }
-    Team::sync();
+    tm.sync();
     for (int idx = tr; idx < n * n; idx += ts) Q[idx] = dfa::to_double(Qn[idx]);   // same 8 bytes per element
-    Team::sync();
+    tm.sync();
   }
   {
-    for (int idx = tr; idx < n * n; idx += ts) {
-      const int i = idx % n, j = idx / n;
+    // Q^T Q is symmetric: one dot product per entry of its upper triangle (i <= j),
+    // enumerated densely so that no lane of an FP64 instruction idles
+    const int ntri = n * (n + 1) / 2;
+    for (int idx = tr; idx < ntri; idx += ts) {
+      int j = (int)((sqrtf(8.f * (float)idx + 1.f) - 1.f) * 0.5f);
+      while (j * (j + 1) / 2 > idx) --j;
+      while ((j + 1) * (j + 2) / 2 <= idx) ++j;
+      const int i = idx - j * (j + 1) / 2;
       const double* qi = Q + (size_t)i * n;
       const double* qj = Q + (size_t)j * n;
       double acc = 0.0;
       for (int k = 0; k < n; ++k) acc = fma(qi[k], qj[k], acc);
-      T[idx] = (i == j ? 1.5 : 0.0) - 0.5 * acc;
+      const double v = (i == j ? 1.5 : 0.0) - 0.5 * acc;
+      T[(size_t)j * n + i] = v;
+      T[(size_t)i * n + j] = v;
     }
-    Team::sync();
+    tm.sync();
     for (int idx = tr; idx < n * n; idx += ts) {
       const int row = idx % n, col = idx / n;
       double acc = 0.0;
       for (int k = 0; k < n; ++k) acc = fma(Q[(size_t)k * n + row], T[(size_t)col * n + k], acc);
       W[idx] = acc;                                // W used as temporary (m*n >= n*n)
     }
-    Team::sync();
+    tm.sync();
     for (int idx = tr; idx < n * n; idx += ts) Q[idx] = W[idx];
-    Team::sync();
+    tm.sync();
   }
   // ---- W = Bm Q in double-float: Bm converted in place (the caller no longer needs it),
   // Q copied to double-float in T; W comes back to FP64 in place.  Its error (about
@@ -304,7 +336,7 @@ __device__ int block_svd(const double* __restrict__ Bm, double* __restrict__ W, 
       Bd[idx] = dfa::from_double(b);
     }
     for (int idx = tr; idx < n * n; idx += ts) Qd[idx] = dfa::from_double(Q[idx]);
-    Team::sync();
+    tm.sync();
     for (int idx = tr; idx < m * n; idx += ts) {
       const int row = idx % m, col = idx / m;
       const float2* qc = Qd + (size_t)col * n;
@@ -312,14 +344,23 @@ __device__ int block_svd(const double* __restrict__ Bm, double* __restrict__ W, 
       for (int k = 0; k < n; ++k) acc = dfa::fma(Bd[(size_t)k * m + row], qc[k], acc);
       Wd[idx] = acc;
     }
-    Team::sync();
+    tm.sync();
     for (int idx = tr; idx < m * n; idx += ts) W[idx] = dfa::to_double(Wd[idx]);
-    Team::sync();
+    tm.sync();
   }
   if (n < 2) return noconv;
   // ---- FP64 phase.  A sweep that finds no pair above 1e-7 relative leaves
   // off-diagonals near 1e-14 after its own rotations (quadratic convergence),
   // so the loop ends after that sweep without a confirming one.
+  double* nrm = T;                                 // squared column norms (T is free from here on)
+  for (int j = grp; j < n; j += ngrp) {
+    const double* x = W + (size_t)j * m;
+    double a = 0.0;
+    for (int t = gl; t < m; t += 8) a = fma(x[t], x[t], a);
+    a = grp8_sum(a, gmask);
+    if (gl == 0) nrm[j] = a;
+  }
+  tm.sync();
   const double tol64 = 2.220446049250313e-16 * (double)m;
   const float tol64sq = (float)(tol64 * tol64);
   noconv = 1;
@@ -333,15 +374,19 @@ __device__ int block_svd(const double* __restrict__ Bm, double* __restrict__ W, 
         if (i >= n || j >= n) continue;
         double* x = W + (size_t)i * m;
         double* y = W + (size_t)j * m;
-        double al = 0.0, be = 0.0, ga = 0.0;
-        for (int t = gl; t < m; t += 8) {
-          const double xv = x[t], yv = y[t];
-          al = fma(xv, xv, al);
-          be = fma(yv, yv, be);
-          ga = fma(xv, yv, ga);
+        // only lane 0 of the group touches nrm[i], nrm[j]; the group gets them by shuffle
+        double al, be;
+        {
+          double a0 = 0.0, b0 = 0.0;
+          if (gl == 0) {
+            a0 = nrm[i];
+            b0 = nrm[j];
+          }
+          al = __shfl_sync(gmask, a0, lane & ~7);
+          be = __shfl_sync(gmask, b0, lane & ~7);
         }
-        al = grp8_sum(al, gmask);
-        be = grp8_sum(be, gmask);
+        double ga = 0.0;
+        for (int t = gl; t < m; t += 8) ga = fma(x[t], y[t], ga);
         ga = grp8_sum(ga, gmask);
         // columns below 1e-125 of the block's largest entry are zero at this precision
         if (ga == 0.0 || al < 1e-250 || be < 1e-250) continue;
@@ -357,30 +402,75 @@ __device__ int block_svd(const double* __restrict__ Bm, double* __restrict__ W, 
         c = c * fma(-0.5 * w, c * c, 1.5);
         const double s = t * c;
         if (s == 0.0) continue;
-        for (int u = gl; u < m; u += 8) {
-          const double xv = x[u], yv = y[u];
-          x[u] = c * xv - s * yv;
-          y[u] = s * xv + c * yv;
+        if (c == 1.0) {                            // |t| < 2^-27: the rotation is I + s J
+          for (int u = gl; u < m; u += 8) {
+            const double xv = x[u], yv = y[u];
+            x[u] = fma(-s, yv, xv);
+            y[u] = fma(s, xv, yv);
+          }
+        } else {
+          for (int u = gl; u < m; u += 8) {
+            const double xv = x[u], yv = y[u];
+            x[u] = c * xv - s * yv;
+            y[u] = s * xv + c * yv;
+          }
         }
         double* qx = Q + (size_t)i * n;
         double* qy = Q + (size_t)j * n;
-        for (int u = gl; u < n; u += 8) {
-          const double xv = qx[u], yv = qy[u];
-          qx[u] = c * xv - s * yv;
-          qy[u] = s * xv + c * yv;
+        if (c == 1.0) {
+          for (int u = gl; u < n; u += 8) {
+            const double xv = qx[u], yv = qy[u];
+            qx[u] = fma(-s, yv, xv);
+            qy[u] = fma(s, xv, yv);
+          }
+        } else {
+          for (int u = gl; u < n; u += 8) {
+            const double xv = qx[u], yv = qy[u];
+            qx[u] = c * xv - s * yv;
+            qy[u] = s * xv + c * yv;
+          }
+        }
+        // |c x - s y|^2 and |s x + c y|^2 from the Gram entries.  The update carries
+        // the dot product's error (about m eps |x||y|) into the smaller norm, divided
+        // by the fraction of its terms that survives: where less than half survives
+        // (pairs far from orthogonal, e.g. the noise columns of a rank-deficient
+        // block, which keep rotating for several sweeps) that norm is summed again.
+        const double cc = c * c, ss = s * s, g2 = 2.0 * c * s * ga;
+        double na = fma(cc, al, fma(ss, be, -g2));
+        double nb2 = fma(ss, al, fma(cc, be, g2));
+        if (!(na > 0.5 * (cc * al + ss * be + fabs(g2)))) {
+          double acc = 0.0;
+          for (int u = gl; u < m; u += 8) acc = fma(x[u], x[u], acc);
+          na = grp8_sum(acc, gmask);
+        }
+        if (!(nb2 > 0.5 * (ss * al + cc * be + fabs(g2)))) {
+          double acc = 0.0;
+          for (int u = gl; u < m; u += 8) acc = fma(y[u], y[u], acc);
+          nb2 = grp8_sum(acc, gmask);
+        }
+        if (gl == 0) {
+          nrm[i] = na;
+          nrm[j] = nb2;
         }
         rot = 1;
       }
-      Team::sync();
+      tm.sync();
     }
-    worst = Team::max(worst, fscratch);
-    if (!Team::any(rot) || worst <= 1e-14f) {
+    worst = tm.max(worst);
+    if (!tm.any(rot) || worst <= 1e-14f) {
       noconv = 0;
       break;
     }
   }
   return noconv;
 }
+
+// Large SVD blocks run concurrently, one per team of ROT_TEAM_WARPS warps.
+constexpr int ROT_TEAMS = 4;
+constexpr int ROT_TEAM_WARPS = RT_WARPS / ROT_TEAMS;
+constexpr int ROT_TEAM_THREADS = ROT_TEAM_WARPS * 32;
+static_assert(ROT_TEAMS * ROT_TEAM_WARPS == RT_WARPS, "teams must tile the CTA");
+static_assert(ROT_TEAMS <= 15, "one named barrier per team");
 
 __global__ void __launch_bounds__(RT_THREADS) rotate_pairs_kernel(const RotDesc* __restrict__ descs) {
   const RotDesc& D = descs[blockIdx.x];
@@ -396,7 +486,8 @@ __global__ void __launch_bounds__(RT_THREADS) rotate_pairs_kernel(const RotDesc*
   __shared__ unsigned char sig_keep[MAXSIG];
   __shared__ short s_ord[MAXBLK];
   __shared__ int s_nblk, s_nnew, s_total, s_nsig, s_keep, s_status, s_nbig;
-  __shared__ float s_fmax;
+  __shared__ float s_tscr[ROT_TEAMS];
+  __shared__ int s_tbi[ROT_TEAMS], s_next_big, s_next_small;
   __shared__ double s_disc, s_red[RT_WARPS], s_flops;
 
   ThetaBlk* tb = reinterpret_cast<ThetaBlk*>(D.meta);
@@ -570,8 +661,10 @@ __global__ void __launch_bounds__(RT_THREADS) rotate_pairs_kernel(const RotDesc*
       s_ord[rank] = (short)b;
     }
     __syncthreads();
-    // ---- SVD of every block: large blocks by the whole CTA one after another,
-    // the rest one warp per block
+    // ---- SVD of every block.  Large blocks go to teams of warps, each team
+    // taking the next block from a shared counter (largest first); a team with
+    // nothing left and every warp afterwards take the small blocks one warp per
+    // block from a second counter.
     if (tid == 0) {
       int nb_big = 0;
       while (nb_big < nnew) {
@@ -580,67 +673,83 @@ __global__ void __launch_bounds__(RT_THREADS) rotate_pairs_kernel(const RotDesc*
         ++nb_big;
       }
       s_nbig = nb_big;
+      s_next_big = 0;
+      s_next_small = 0;
     }
     __syncthreads();
     const int nbig = s_nbig;
-    for (int bi = 0; bi < nbig; ++bi) {
-      const int b = s_ord[bi];
-      const NewBlk B = nb[b];
-      const bool trans = B.nc > B.nr;
-      const int m = trans ? B.nc : B.nr, n = trans ? B.nr : B.nc;
-      double* Bm = D.bbuf + B.wofs;
-      double* W = D.wbuf + B.wofs;
-      float* W32 = D.w32 + B.wofs;
-      double* Q = D.qbuf + B.qofs;
-      double* T = D.tbuf + B.qofs;
-      float* Q32 = D.q32 + B.qofs;
-      double mx = 0.0;
-      for (int idx = tid; idx < m * n; idx += RT_THREADS) {
-        const int wi = idx % m, wj = idx / m;
-        const int br = trans ? wj : wi, bc = trans ? wi : wj;
-        int k1p = 3, k2p = 3;
-        while (k1p > 0 && (B.rowsec[k1p] < 0 || B.rowoff[k1p] > br)) --k1p;
-        while (k2p > 0 && (B.colsec[k2p] < 0 || B.coloff[k2p] > bc)) --k2p;
-        const int sL = B.rowsec[k1p], sR = B.colsec[k2p];
-        const int l = secL.off[sL] + (br - B.rowoff[k1p]);
-        const int r = secR.off[sR] + (bc - B.coloff[k2p]);
-        const int Kp = k1p * 4 + k2p;
-        double acc = 0.0;
-        for (int e = 0; e < gnz_n[Kp]; ++e) {
-          const int K = gnz_k[Kp][e];
-          const int k1 = K >> 2, k2 = K & 3;
-          const int qM = qadd(secL.q[sL], local_charge(k1));
-          if (qM < 0 || lutM[qM] < 0) continue;
-          acc = fma(gnz_v[Kp][e], D.theta[(((size_t)l * 4 + k1) * 4 + k2) * chr + r], acc);
+    {
+      const int team = warp / ROT_TEAM_WARPS, twarp = warp % ROT_TEAM_WARPS;
+      const SubTeam tm{team * ROT_TEAM_THREADS, ROT_TEAM_THREADS, 1 + team, &s_tscr[team]};
+      const int trk = tm.rank();
+      for (;;) {
+        if (trk == 0) s_tbi[team] = atomicAdd(&s_next_big, 1);
+        tm.sync();
+        const int bi = s_tbi[team];
+        tm.sync();
+        if (bi >= nbig) break;
+        const int b = s_ord[bi];
+        const NewBlk B = nb[b];
+        const bool trans = B.nc > B.nr;
+        const int m = trans ? B.nc : B.nr, n = trans ? B.nr : B.nc;
+        double* Bm = D.bbuf + B.wofs;
+        double* W = D.wbuf + B.wofs;
+        float* W32 = D.w32 + B.wofs;
+        double* Q = D.qbuf + B.qofs;
+        double* T = D.tbuf + B.qofs;
+        float* Q32 = D.q32 + B.qofs;
+        double mx = 0.0;
+        for (int idx = trk; idx < m * n; idx += ROT_TEAM_THREADS) {
+          const int wi = idx % m, wj = idx / m;
+          const int br = trans ? wj : wi, bc = trans ? wi : wj;
+          int k1p = 3, k2p = 3;
+          while (k1p > 0 && (B.rowsec[k1p] < 0 || B.rowoff[k1p] > br)) --k1p;
+          while (k2p > 0 && (B.colsec[k2p] < 0 || B.coloff[k2p] > bc)) --k2p;
+          const int sL = B.rowsec[k1p], sR = B.colsec[k2p];
+          const int l = secL.off[sL] + (br - B.rowoff[k1p]);
+          const int r = secR.off[sR] + (bc - B.coloff[k2p]);
+          const int Kp = k1p * 4 + k2p;
+          double acc = 0.0;
+          for (int e = 0; e < gnz_n[Kp]; ++e) {
+            const int K = gnz_k[Kp][e];
+            const int k1 = K >> 2, k2 = K & 3;
+            const int qM = qadd(secL.q[sL], local_charge(k1));
+            if (qM < 0 || lutM[qM] < 0) continue;
+            acc = fma(gnz_v[Kp][e], D.theta[(((size_t)l * 4 + k1) * 4 + k2) * chr + r], acc);
+          }
+          Bm[idx] = acc;
+          mx = fmax(mx, fabs(acc));
         }
-        Bm[idx] = acc;
-        mx = fmax(mx, fabs(acc));
-      }
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-      if (lane == 0) s_red[warp] = mx;
-      __syncthreads();
-      double bmax = 0.0;
-      for (int w2 = 0; w2 < RT_WARPS; ++w2) bmax = fmax(bmax, s_red[w2]);
-      const double scale = bmax > 0.0 ? bmax : 1.0;
-      const double inv = 1.0 / scale;
-      for (int idx = tid; idx < m * n; idx += RT_THREADS) Bm[idx] *= inv;
-      if (tid == 0) nb[b].scale = scale;
-      __syncthreads();
-      const int ncv = block_svd<CtaTeam>(Bm, W, Q, W32, Q32, T, m, n, D.max_sweeps, &s_fmax);
-      if (ncv && tid == 0) atomicOr(&s_status, STATUS_NOCONV | (min(m, 4095) << 8) | (min(n, 4095) << 20));
-      for (int j = warp; j < n; j += RT_WARPS) {
-        double acc = 0.0;
-        for (int u = lane; u < m; u += 32) {
-          const double v = W[(size_t)j * m + u];
-          acc = fma(v, v, acc);
+        for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if (lane == 0) s_red[warp] = mx;
+        tm.sync();
+        double bmax = 0.0;
+        for (int w2 = 0; w2 < ROT_TEAM_WARPS; ++w2) bmax = fmax(bmax, s_red[team * ROT_TEAM_WARPS + w2]);
+        const double scale = bmax > 0.0 ? bmax : 1.0;
+        const double inv = 1.0 / scale;
+        for (int idx = trk; idx < m * n; idx += ROT_TEAM_THREADS) Bm[idx] *= inv;
+        if (trk == 0) nb[b].scale = scale;
+        tm.sync();
+        const int ncv = block_svd(tm, Bm, W, Q, W32, Q32, T, m, n, D.max_sweeps);
+        if (ncv && trk == 0) atomicOr(&s_status, STATUS_NOCONV | (min(m, 4095) << 8) | (min(n, 4095) << 20));
+        for (int j = twarp; j < n; j += ROT_TEAM_WARPS) {
+          double acc = 0.0;
+          for (int u = lane; u < m; u += 32) {
+            const double v = W[(size_t)j * m + u];
+            acc = fma(v, v, acc);
+          }
+          acc = warp_sum(acc);
+          if (lane == 0) sig[B.sofs + j] = sqrt(acc) * scale;
         }
-        acc = warp_sum(acc);
-        if (lane == 0) sig[B.sofs + j] = sqrt(acc) * scale;
       }
-      __syncthreads();
     }
-    for (int bi = nbig + warp; bi < nnew; bi += RT_WARPS) {
+    const WarpTeam wt;
+    for (;;) {
+      int bi = 0;
+      if (lane == 0) bi = atomicAdd(&s_next_small, 1);
+      bi = __shfl_sync(0xffffffffu, bi, 0) + nbig;
+      if (bi >= nnew) break;
       const int b = s_ord[bi];
       const NewBlk B = nb[b];
       const bool trans = B.nc > B.nr;                // work on B^T so that n <= m
@@ -681,7 +790,7 @@ __global__ void __launch_bounds__(RT_THREADS) rotate_pairs_kernel(const RotDesc*
       for (int idx = lane; idx < m * n; idx += 32) Bm[idx] *= inv;
       if (lane == 0) nb[b].scale = scale;
       __syncwarp();
-      const int ncv = block_svd<WarpTeam>(Bm, W, Q, W32, Q32, T, m, n, D.max_sweeps, nullptr);
+      const int ncv = block_svd(wt, Bm, W, Q, W32, Q32, T, m, n, D.max_sweeps);
       if (ncv && lane == 0) atomicOr(&s_status, STATUS_NOCONV | (min(m, 4095) << 8) | (min(n, 4095) << 20));
       for (int j = 0; j < n; ++j) {
         double acc = 0.0;
