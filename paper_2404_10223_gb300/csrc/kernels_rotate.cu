@@ -124,7 +124,10 @@ __device__ int jacobi_block(double* W, double* Q, int m, int n, int max_sweeps, 
 constexpr int RT_THREADS = 512;
 constexpr int RT_WARPS = RT_THREADS / 32;
 constexpr int MAXBLK = 1024;
-constexpr int BIG_BLOCK_N = 24;    // blocks with min(rows, cols) >= this use the whole CTA
+#ifndef TNQE_ROT_BIG_BLOCK_N
+#define TNQE_ROT_BIG_BLOCK_N 24
+#endif
+constexpr int BIG_BLOCK_N = TNQE_ROT_BIG_BLOCK_N;   // blocks with min(rows, cols) >= this go to warp teams
 
 __device__ __forceinline__ float grp8_sum(float v, unsigned mask) {
   v += __shfl_xor_sync(mask, v, 4);
@@ -202,8 +205,9 @@ struct SubTeam {
 // dot product per column pair (gamma = x.y): the squared column norms are
 // computed once and carried through every rotation by the exact 2 x 2 Gram
 // update (summed again from the column where that update cancels, so each
-// carried norm keeps a relative error of a few m eps per rotation), and a
-// rotation whose cosine rounds to 1 costs one FMA per element.
+// carried norm keeps a relative error of a few m eps per rotation), the scalar
+// work of a pair runs on one thread, and a rotation whose cosine rounds to 1
+// costs one FMA per element.
 template <class Team>
 __device__ int block_svd(const Team& tm, const double* __restrict__ Bm, double* __restrict__ W,
                          double* __restrict__ Q, float* __restrict__ W32, float* __restrict__ Q32,
@@ -352,7 +356,16 @@ __device__ int block_svd(const Team& tm, const double* __restrict__ Bm, double* 
   // ---- FP64 phase.  A sweep that finds no pair above 1e-7 relative leaves
   // off-diagonals near 1e-14 after its own rotations (quadratic convergence),
   // so the loop ends after that sweep without a confirming one.
+  //
+  // Every round takes three steps: the 8-lane groups form gamma = x.y of their
+  // column pairs; one thread per pair turns (alpha, beta, gamma) into the
+  // rotation and the new norms; the groups apply the rotations.  The per-pair
+  // scalar FP64 work (angle, cosine, norm update) thus fills whole warp
+  // instructions with 32 pairs instead of 4.
   double* nrm = T;                                 // squared column norms (T is free from here on)
+  double* gam = const_cast<double*>(Bm);           // per pair of a round: gamma, then a recompute code
+  double* cv = gam + n2 / 2;                       // cos, sin per pair (Bm is free: m n >= 3 n2 / 2)
+  double* sv = cv + n2 / 2;
   for (int j = grp; j < n; j += ngrp) {
     const double* x = W + (size_t)j * m;
     double a = 0.0;
@@ -372,41 +385,83 @@ __device__ int block_svd(const Team& tm, const double* __restrict__ Bm, double* 
         int i, j;
         tour_pair(r, k, n2, i, j);
         if (i >= n || j >= n) continue;
-        double* x = W + (size_t)i * m;
-        double* y = W + (size_t)j * m;
-        // only lane 0 of the group touches nrm[i], nrm[j]; the group gets them by shuffle
-        double al, be;
-        {
-          double a0 = 0.0, b0 = 0.0;
-          if (gl == 0) {
-            a0 = nrm[i];
-            b0 = nrm[j];
-          }
-          al = __shfl_sync(gmask, a0, lane & ~7);
-          be = __shfl_sync(gmask, b0, lane & ~7);
-        }
+        const double* x = W + (size_t)i * m;
+        const double* y = W + (size_t)j * m;
         double ga = 0.0;
         for (int t = gl; t < m; t += 8) ga = fma(x[t], y[t], ga);
         ga = grp8_sum(ga, gmask);
-        // columns below 1e-125 of the block's largest entry are zero at this precision
-        if (ga == 0.0 || al < 1e-250 || be < 1e-250) continue;
-        const double sc = exp2_neg_exponent(fmax(al, be));
-        const float af = (float)(al * sc), bf = (float)(be * sc), gf = (float)(ga * sc);
-        if (!(gf * gf > tol64sq * af * bf)) continue;
-        worst = fmaxf(worst, (gf * gf) / (af * bf));
-        const float zeta = (bf - af) / (2.f * gf);
-        const float t32 = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + hypotf(1.f, zeta));
-        const double t = (double)t32, w = fma(t, t, 1.0);
-        double c = (double)rsqrtf((float)w);
-        c = c * fma(-0.5 * w, c * c, 1.5);
-        c = c * fma(-0.5 * w, c * c, 1.5);
-        const double s = t * c;
+        if (gl == 0) gam[k] = ga;
+      }
+      tm.sync();
+      for (int k = tr; k < n2 / 2; k += ts) {
+        int i, j;
+        tour_pair(r, k, n2, i, j);
+        double c = 1.0, s = 0.0, code = 0.0;
+        if (i < n && j < n) {
+          const double al = nrm[i], be = nrm[j], ga = gam[k];
+          // columns below 1e-125 of the block's largest entry are zero at this precision
+          if (ga != 0.0 && al >= 1e-250 && be >= 1e-250) {
+            const double sc = exp2_neg_exponent(fmax(al, be));
+            const float af = (float)(al * sc), bf = (float)(be * sc), gf = (float)(ga * sc);
+            if (gf * gf > tol64sq * af * bf) {
+              worst = fmaxf(worst, (gf * gf) / (af * bf));
+              const float zeta = (bf - af) / (2.f * gf);
+              const float t32 = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + hypotf(1.f, zeta));
+              const double t = (double)t32;
+              if (fabsf(t32) < 7.0e-9f) {            // 1 + t^2 rounds to 1: the rotation is I + t J
+                s = t;
+              } else {
+                const double w = fma(t, t, 1.0);
+                c = (double)rsqrtf((float)w);
+                c = c * fma(-0.5 * w, c * c, 1.5);
+                c = c * fma(-0.5 * w, c * c, 1.5);
+                s = t * c;
+              }
+              if (s != 0.0) {
+                rot = 1;
+                // |c x - s y|^2 and |s x + c y|^2 from the Gram entries.  The update carries
+                // the dot product's error (about m eps |x||y|) into the smaller norm, divided
+                // by the fraction of its terms that survives: where less than half survives
+                // (pairs far from orthogonal, e.g. the noise columns of a rank-deficient
+                // block, which keep rotating for several sweeps) the rotating group sums that
+                // norm again.
+                const double cc = c * c, ss = s * s, g2 = 2.0 * c * s * ga;
+                const double na = fma(cc, al, fma(ss, be, -g2));
+                const double nb2 = fma(ss, al, fma(cc, be, g2));
+                const bool ri = !(na > 0.5 * (cc * al + ss * be + fabs(g2)));
+                const bool rj = !(nb2 > 0.5 * (ss * al + cc * be + fabs(g2)));
+                nrm[i] = na;
+                nrm[j] = nb2;
+                code = (ri ? 1.0 : 0.0) + (rj ? 2.0 : 0.0);
+              }
+            }
+          }
+        }
+        cv[k] = c;
+        sv[k] = s;
+        gam[k] = code;
+      }
+      tm.sync();
+      for (int k = grp; k < n2 / 2; k += ngrp) {
+        const double s = sv[k];
         if (s == 0.0) continue;
-        if (c == 1.0) {                            // |t| < 2^-27: the rotation is I + s J
+        const double c = cv[k];
+        int i, j;
+        tour_pair(r, k, n2, i, j);
+        double* x = W + (size_t)i * m;
+        double* y = W + (size_t)j * m;
+        double* qx = Q + (size_t)i * n;
+        double* qy = Q + (size_t)j * n;
+        if (c == 1.0) {
           for (int u = gl; u < m; u += 8) {
             const double xv = x[u], yv = y[u];
             x[u] = fma(-s, yv, xv);
             y[u] = fma(s, xv, yv);
+          }
+          for (int u = gl; u < n; u += 8) {
+            const double xv = qx[u], yv = qy[u];
+            qx[u] = fma(-s, yv, xv);
+            qy[u] = fma(s, xv, yv);
           }
         } else {
           for (int u = gl; u < m; u += 8) {
@@ -414,45 +469,28 @@ __device__ int block_svd(const Team& tm, const double* __restrict__ Bm, double* 
             x[u] = c * xv - s * yv;
             y[u] = s * xv + c * yv;
           }
-        }
-        double* qx = Q + (size_t)i * n;
-        double* qy = Q + (size_t)j * n;
-        if (c == 1.0) {
-          for (int u = gl; u < n; u += 8) {
-            const double xv = qx[u], yv = qy[u];
-            qx[u] = fma(-s, yv, xv);
-            qy[u] = fma(s, xv, yv);
-          }
-        } else {
           for (int u = gl; u < n; u += 8) {
             const double xv = qx[u], yv = qy[u];
             qx[u] = c * xv - s * yv;
             qy[u] = s * xv + c * yv;
           }
         }
-        // |c x - s y|^2 and |s x + c y|^2 from the Gram entries.  The update carries
-        // the dot product's error (about m eps |x||y|) into the smaller norm, divided
-        // by the fraction of its terms that survives: where less than half survives
-        // (pairs far from orthogonal, e.g. the noise columns of a rank-deficient
-        // block, which keep rotating for several sweeps) that norm is summed again.
-        const double cc = c * c, ss = s * s, g2 = 2.0 * c * s * ga;
-        double na = fma(cc, al, fma(ss, be, -g2));
-        double nb2 = fma(ss, al, fma(cc, be, g2));
-        if (!(na > 0.5 * (cc * al + ss * be + fabs(g2)))) {
-          double acc = 0.0;
-          for (int u = gl; u < m; u += 8) acc = fma(x[u], x[u], acc);
-          na = grp8_sum(acc, gmask);
+        const double code = gam[k];
+        if (code != 0.0) {
+          const int cd = (int)code;
+          if (cd & 1) {
+            double acc = 0.0;
+            for (int u = gl; u < m; u += 8) acc = fma(x[u], x[u], acc);
+            acc = grp8_sum(acc, gmask);
+            if (gl == 0) nrm[i] = acc;
+          }
+          if (cd & 2) {
+            double acc = 0.0;
+            for (int u = gl; u < m; u += 8) acc = fma(y[u], y[u], acc);
+            acc = grp8_sum(acc, gmask);
+            if (gl == 0) nrm[j] = acc;
+          }
         }
-        if (!(nb2 > 0.5 * (ss * al + cc * be + fabs(g2)))) {
-          double acc = 0.0;
-          for (int u = gl; u < m; u += 8) acc = fma(y[u], y[u], acc);
-          nb2 = grp8_sum(acc, gmask);
-        }
-        if (gl == 0) {
-          nrm[i] = na;
-          nrm[j] = nb2;
-        }
-        rot = 1;
       }
       tm.sync();
     }
@@ -466,7 +504,10 @@ __device__ int block_svd(const Team& tm, const double* __restrict__ Bm, double* 
 }
 
 // Large SVD blocks run concurrently, one per team of ROT_TEAM_WARPS warps.
-constexpr int ROT_TEAMS = 4;
+#ifndef TNQE_ROT_TEAMS
+#define TNQE_ROT_TEAMS 4
+#endif
+constexpr int ROT_TEAMS = TNQE_ROT_TEAMS;
 constexpr int ROT_TEAM_WARPS = RT_WARPS / ROT_TEAMS;
 constexpr int ROT_TEAM_THREADS = ROT_TEAM_WARPS * 32;
 static_assert(ROT_TEAMS * ROT_TEAM_WARPS == RT_WARPS, "teams must tile the CTA");
