@@ -99,6 +99,7 @@ struct DevMps {
   std::vector<double*> d_val;
   std::vector<float*> d_val32;
   std::vector<float2*> d_valdf;          // (hi, lo) FP32 pairs of the MPO values
+  std::vector<float4*> d_ent;            // (hi, lo, column bits, 0) per MPO nonzero
   std::vector<void*> owned;
   void free_all() {
     for (void* p : owned) cudaFree(p);
@@ -1055,6 +1056,7 @@ void run_contractions_oz(tnqe_ctx* c, const std::vector<std::pair<int, int>>& pa
         s.rowperm = bi.d_rowperm[t];
         s.col = bi.d_col[t];
         s.val = bi.d_valdf[t];
+        s.ent = bi.d_ent[t];
         s.X = X[w];
         s.Y = Y[w];
         sppre.push_back(tasks);
@@ -1440,6 +1442,14 @@ void prepare_mps(tnqe_ctx* c, const double* const* tensors, const int* bond_dims
       vdf[e].y = (float)(v - (double)vdf[e].x);
     }
     m.d_valdf.push_back(dalloc_copy(vdf, m.owned));
+    std::vector<float4> ent(vdf.size());
+    for (size_t e = 0; e < vdf.size(); ++e) {
+      int col = m.mpo.sites[t].col[e];
+      float cf;
+      std::memcpy(&cf, &col, sizeof(cf));
+      ent[e] = make_float4(vdf[e].x, vdf[e].y, cf, 0.f);
+    }
+    m.d_ent.push_back(dalloc_copy(ent, m.owned));
   }
 }
 

@@ -149,6 +149,7 @@ struct SpmmDfDesc {               // Y[a][row][:] = sum val * X[a][col][:] in do
   const int* rowperm;             // rows by descending nonzero count
   const int* col;
   const float2* val;
+  const float4* ent;              // per nonzero: (value hi, value lo, column as int bits, 0)
   const float2* X;
   float2* Y;
 };

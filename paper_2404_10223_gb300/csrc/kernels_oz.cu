@@ -211,15 +211,38 @@ __global__ void __launch_bounds__(256) spmm_df_kernel(const SpmmDfDesc* __restri
   }
 }
 
+// (ah, al) += (vh, vl) * (xh, xl) with the cross terms fused: 12 FP32 operations
+__device__ __forceinline__ void df_fma_fused(float vh, float vl, float xh, float xl, float& ah, float& al) {
+  const float p = __fmul_rn(vh, xh);
+  const float pe = fmaf(vh, xl, fmaf(vl, xh, fmaf(vh, xh, -p)));
+  float s, e;
+  two_sum_rn(ah, p, s, e);
+  ah = s;
+  al = __fadd_rn(al, __fadd_rn(e, pe));
+}
+
 // Y[a][row][b0:b0+BW] for every row, with X[a][:][b0:b0+BW] staged in shared
-// memory once (each X element is read by every nonzero of its column).
-// Threads take (row, column) pairs; rows go in descending nonzero count so the
-// BW-lane groups of a warp carry similar loop lengths.
+// memory once (each X element is read by every nonzero of its column).  The
+// slab arrives by cp.async, 16 bytes per copy where the rows allow it, so a
+// CTA keeps its whole slab in flight instead of one element per thread.  Each
+// thread then owns one row and all BW columns: BW independent double-float
+// accumulations share every (value, column) load, and rows go in descending
+// nonzero count so the threads of a warp run loops of similar length.
 constexpr int SPMM_SMEM_BYTES = 112 * 1024;
-template <int BW>
-__global__ void __launch_bounds__(256, 2) spmm_df_smem_kernel(const SpmmDfDesc* __restrict__ descs,
-                                                           const long long* __restrict__ prefix, int nprob) {
-  extern __shared__ float2 xs[];
+constexpr int SPMM_THREADS = 256;
+__device__ __forceinline__ void cp_async_zfill(void* dst, const void* src, int cp_bytes16, int src_bytes) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  if (cp_bytes16)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(src_bytes) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src), "r"(src_bytes) : "memory");
+}
+template <int BW, int TPR>
+__global__ void __launch_bounds__(SPMM_THREADS, 2) spmm_df_smem_kernel(const SpmmDfDesc* __restrict__ descs,
+                                                                    const long long* __restrict__ prefix, int nprob) {
+  extern __shared__ __align__(16) float2 xs[];
+  constexpr int NC = BW / TPR;                   // columns per thread: c, c + TPR, ...
+  constexpr int RPP = SPMM_THREADS / TPR;        // rows per pass
   const long long task = blockIdx.x;
   const int p = find_prob(prefix, nprob, task);
   const SpmmDfDesc& d = descs[p];
@@ -227,37 +250,49 @@ __global__ void __launch_bounds__(256, 2) spmm_df_smem_kernel(const SpmmDfDesc* 
   const long long local = task - prefix[p];
   const int a = (int)(local / nbt), b0 = (int)(local % nbt) * BW;
   const int tid = threadIdx.x;
-  const float2* Xa = d.X + (long long)a * d.ncols_x * d.width + b0;
-  for (int i = tid; i < d.ncols_x * BW; i += 256) {
-    const int r = i / BW, c = i % BW;
-    xs[i] = (b0 + c < d.width) ? Xa[(long long)r * d.width + c] : make_float2(0.f, 0.f);
+  const int width = d.width, ncols = d.ncols_x;
+  const float2* Xa = d.X + (long long)a * ncols * width + b0;
+  if (BW >= 2 && (width & 1) == 0 && (reinterpret_cast<size_t>(Xa) & 15) == 0) {
+    constexpr int CPR = BW / 2;                  // 16-byte copies per slab row
+    for (int i = tid; i < ncols * CPR; i += SPMM_THREADS) {
+      const int r = i / CPR, q = i - r * CPR;
+      const int c0 = b0 + 2 * q;
+      const int bytes = c0 + 2 <= width ? 16 : (c0 < width ? 8 : 0);
+      const float2* src = bytes ? Xa + (long long)r * width + 2 * q : Xa;
+      cp_async_zfill(xs + r * BW + 2 * q, src, 1, bytes);
+    }
+  } else {
+    for (int i = tid; i < ncols * BW; i += SPMM_THREADS) {
+      const int r = i / BW, c = i - r * BW;
+      const int bytes = b0 + c < width ? 8 : 0;
+      const float2* src = bytes ? Xa + (long long)r * width + c : Xa;
+      cp_async_zfill(xs + i, src, 0, bytes);
+    }
   }
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
   __syncthreads();
-  // each thread: one row, NC columns c, c + HW, ... (independent accumulations, shared index loads)
-  constexpr int NC = BW < 2 ? BW : 2;
-  constexpr int HW = BW / NC;
-  const int c = tid % HW;
-  float2* Ya = d.Y + (long long)a * d.nrows * d.width + b0;
-  for (int r0 = 0; r0 < d.nrows; r0 += 256 / HW) {
-    const int rr = r0 + tid / HW;
-    if (rr >= d.nrows) break;
+  float2* Ya = d.Y + (long long)a * d.nrows * width + b0;
+  const float4* __restrict__ ent = d.ent;
+  const int c = tid % TPR;
+  for (int rr = tid / TPR; rr < d.nrows; rr += RPP) {
     const int row = d.rowperm[rr];
     const int e0 = d.rowptr[row], e1 = d.rowptr[row + 1];
     float ah[NC], al[NC];
 #pragma unroll
     for (int u = 0; u < NC; ++u) ah[u] = al[u] = 0.f;
     for (int e = e0; e < e1; ++e) {
-      const float2 v = d.val[e];
-      const float2* xr = xs + d.col[e] * BW + c;
+      const float4 en = __ldg(ent + e);
+      const float2* xr = xs + __float_as_int(en.z) * BW + c;
 #pragma unroll
       for (int u = 0; u < NC; ++u) {
-        const float2 x = xr[u * HW];
-        df_fma(v.x, v.y, x.x, x.y, ah[u], al[u]);
+        const float2 x = xr[u * TPR];
+        df_fma_fused(en.x, en.y, x.x, x.y, ah[u], al[u]);
       }
     }
+    float2* y = Ya + (long long)row * width + c;
 #pragma unroll
     for (int u = 0; u < NC; ++u)
-      if (b0 + c + u * HW < d.width) Ya[(long long)row * d.width + c + u * HW] = df_norm(ah[u], al[u]);
+      if (b0 + c + u * TPR < width) y[u * TPR] = df_norm(ah[u], al[u]);
   }
 }
 
@@ -309,6 +344,18 @@ int spmm_df_smem_width(int max_ncols_x) {
     if ((long long)max_ncols_x * bw * (long long)sizeof(float2) <= SPMM_SMEM_BYTES) return bw;
   return 0;
 }
+#ifndef TNQE_SPMM_TPR
+#define TNQE_SPMM_TPR 4
+#endif
+template <int BW>
+static cudaError_t launch_spmm_bw(const SpmmDfDesc* d, const long long* prefix, int n, long long blocks, size_t smem,
+                                  cudaStream_t st) {
+  constexpr int TPR = TNQE_SPMM_TPR < BW ? TNQE_SPMM_TPR : BW;
+  cudaError_t e = cudaFuncSetAttribute(spmm_df_smem_kernel<BW, TPR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       SPMM_SMEM_BYTES);
+  if (e == cudaSuccess) spmm_df_smem_kernel<BW, TPR><<<(unsigned)blocks, SPMM_THREADS, smem, st>>>(d, prefix, n);
+  return e;
+}
 int launch_spmm_df_smem(const SpmmDfDesc* d, const long long* prefix, int n, long long blocks, int bw,
                         int max_ncols_x, void* stream) {
   if (blocks <= 0) return 0;
@@ -316,24 +363,10 @@ int launch_spmm_df_smem(const SpmmDfDesc* d, const long long* prefix, int n, lon
   cudaStream_t st = (cudaStream_t)stream;
   cudaError_t e = cudaSuccess;
   switch (bw) {
-    case 8:
-      e = cudaFuncSetAttribute(spmm_df_smem_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, SPMM_SMEM_BYTES);
-      if (e == cudaSuccess) spmm_df_smem_kernel<8><<<(unsigned)blocks, 256, smem, st>>>(d, prefix, n);
-      break;
-    case 4:
-      e = cudaFuncSetAttribute(spmm_df_smem_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, SPMM_SMEM_BYTES);
-      if (e == cudaSuccess) spmm_df_smem_kernel<4><<<(unsigned)blocks, 256, smem, st>>>(d, prefix, n);
-      break;
-    case 2:
-      e = cudaFuncSetAttribute(spmm_df_smem_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, SPMM_SMEM_BYTES);
-      if (e == cudaSuccess) spmm_df_smem_kernel<2><<<(unsigned)blocks, 256, smem, st>>>(d, prefix, n);
-      break;
-    case 1:
-      e = cudaFuncSetAttribute(spmm_df_smem_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, SPMM_SMEM_BYTES);
-      if (e == cudaSuccess) spmm_df_smem_kernel<1><<<(unsigned)blocks, 256, smem, st>>>(d, prefix, n);
-      break;
-    default:
-      return (int)cudaErrorInvalidValue;
+    case 8: e = launch_spmm_bw<8>(d, prefix, n, blocks, smem, st); break;
+    case 4: e = launch_spmm_bw<4>(d, prefix, n, blocks, smem, st); break;
+    case 2: e = launch_spmm_bw<2>(d, prefix, n, blocks, smem, st); break;
+    default: e = launch_spmm_bw<1>(d, prefix, n, blocks, smem, st); break;
   }
   if (e != cudaSuccess) return (int)e;
   return (int)cudaGetLastError();
