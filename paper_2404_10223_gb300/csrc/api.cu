@@ -1015,6 +1015,7 @@ void run_contractions_oz(tnqe_ctx* c, const std::vector<std::pair<int, int>>& pa
     std::vector<OzGemmDesc> g1, g3;
     std::vector<SpmmDfDesc> sp;
     std::vector<long long> sapre, sbpre, g1pre, g3pre, sppre;
+    std::vector<int> sbmaxk(N, 0);        // largest K of the column slicing per site
     double slice_bytes = 0.0;
     for (int t = 0; t < N; ++t) {
       long long rowsA = 0, blocksB = 0, tiles1 = 0, tiles3 = 0, tasks = 0;
@@ -1065,6 +1066,7 @@ void run_contractions_oz(tnqe_ctx* c, const std::vector<std::pair<int, int>>& pa
         // B slices: Y columns (w', b') over (a, k), K-major
         const long long NB = (long long)Dout * cb2;
         SliceColsDesc b{Y[w], Bsl[w], expB[w], NB, ld8(4 * ca), NB * ld8(4 * ca), 4 * ca, (int)NB, ns, 0};
+        sbmaxk[t] = std::max(sbmaxk[t], 4 * ca);
         sbpre.push_back(blocksB);
         blocksB += (NB + 15) / 16;
         sb.push_back(b);
@@ -1154,7 +1156,8 @@ void run_contractions_oz(tnqe_ctx* c, const std::vector<std::pair<int, int>>& pa
       else
         CKL(launch_spmm_df(reinterpret_cast<SpmmDfDesc*>(dd + o_sp) + i, pre(o_spp), nw, sppre[ip + nw], c->stream));
       record_event(c, E[3]);
-      CKL(launch_slice_cols(reinterpret_cast<SliceColsDesc*>(dd + o_sb) + i, pre(o_sbp), nw, sbpre[ip + nw], c->stream));
+      CKL(launch_slice_cols(reinterpret_cast<SliceColsDesc*>(dd + o_sb) + i, pre(o_sbp), nw, sbpre[ip + nw], sbmaxk[t],
+                            c->stream));
       record_event(c, E[4]);
       CKL(launch_gemm_bf16s(reinterpret_cast<OzGemmDesc*>(dd + o_g3) + i, pre(o_g3p), nw, g3pre[ip + nw],
                             c->opt.max_spin, derr, bn3, ns, c->stream));

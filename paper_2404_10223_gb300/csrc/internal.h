@@ -172,7 +172,8 @@ int launch_gemm_tf32x3(const TcGemmDesc* d, const long long* tile_prefix, int np
 int launch_spmm_t_f32(const SpmmTDesc* d, const long long* prefix, int nprob, long long total, void* stream);
 int launch_extract_f32(const float* const* fin, int npairs, int ld, double* H, double* S, void* stream);
 int launch_slice_rows(const SliceRowsDesc* d, const long long* prefix, int n, long long rows, void* stream);
-int launch_slice_cols(const SliceColsDesc* d, const long long* prefix, int n, long long blocks, void* stream);
+int launch_slice_cols(const SliceColsDesc* d, const long long* prefix, int n, long long blocks, int max_k,
+                      void* stream);
 int launch_slice_sites(const SliceSiteDesc* d, const long long* prefix, int n, long long rows, void* stream);
 int launch_spmm_df(const SpmmDfDesc* d, const long long* prefix, int n, long long total, void* stream);
 // shared-memory form: one CTA per (problem, a, bw ket columns); prefix counts CTAs

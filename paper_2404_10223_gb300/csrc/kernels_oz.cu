@@ -52,6 +52,15 @@ __device__ __forceinline__ int find_prob(const long long* prefix, int nprob, lon
 __device__ __forceinline__ int row_exponent_f(float m) { return m > 0.f ? ilogbf(m) + 2 : 0; }
 __device__ __forceinline__ int row_exponent_d(double m) { return m > 0.0 ? ilogb(m) + 2 : 0; }
 
+// cp.async of 16 bytes (cp_bytes16) or 8 bytes; bytes beyond src_bytes are zero-filled
+__device__ __forceinline__ void cp_async_zfill(void* dst, const void* src, int cp_bytes16, int src_bytes) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  if (cp_bytes16)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(src_bytes) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src), "r"(src_bytes) : "memory");
+}
+
 // Slices of one double-float value x = hi + lo (|x| 2^-e < 1/2): out[i] = S_i 2^-(8(i+1)).
 __device__ __forceinline__ void slice_df(float hi, float lo, int e, int ns, __nv_bfloat16* out, long long stride) {
   float th = ldexpf(hi, 8 - e), tl = ldexpf(lo, 8 - e);
@@ -97,10 +106,9 @@ __global__ void __launch_bounds__(256) slice_rows_kernel(const SliceRowsDesc* __
   }
 }
 
-// Columns (w',b') of Y[(a,k)][(w',b')] over K = (a,k), transposed to K-major slices.
-// One CTA per 16 columns of one problem; 256 threads.
-__global__ void __launch_bounds__(256) slice_cols_kernel(const SliceColsDesc* __restrict__ descs,
-                                                         const long long* __restrict__ prefix, int nprob) {
+// The same for K > 1024 (tile too large for shared memory): two passes over global memory.
+__global__ void __launch_bounds__(256) slice_cols_global_kernel(const SliceColsDesc* __restrict__ descs,
+                                                                const long long* __restrict__ prefix, int nprob) {
   __shared__ float2 tile[64][17];
   __shared__ float red[16][17];
   __shared__ int sexp[16];
@@ -139,6 +147,79 @@ __global__ void __launch_bounds__(256) slice_cols_kernel(const SliceColsDesc* __
       }
     }
     __syncthreads();
+  }
+}
+
+// Columns (w',b') of Y[(a,k)][(w',b')] over K = (a,k), transposed to K-major slices.
+// One CTA per 16 columns of one problem; 256 threads.  The K x 16 tile is read
+// from global memory once, by cp.async into shared memory laid out column by
+// column (stride K + 1 elements, so neither the copies nor the reads of one
+// column collide in the banks); the column maxima and all slices come from there.
+constexpr int SLICE_COLS_SMEM_MAX = 16 * (1024 + 1) * 8;
+__global__ void __launch_bounds__(256) slice_cols_kernel(const SliceColsDesc* __restrict__ descs,
+                                                         const long long* __restrict__ prefix, int nprob) {
+  extern __shared__ __align__(16) float2 tl[];
+  __shared__ float red[16][17];
+  __shared__ int sexp[16];
+  const long long task = blockIdx.x;
+  const int p = find_prob(prefix, nprob, task);
+  const SliceColsDesc& d = descs[p];
+  const int c0 = (int)(task - prefix[p]) * 16;
+  const int tid = threadIdx.x, K = d.K, KS = K + 1;
+  const float2* src = d.src + c0;
+  for (int i = tid; i < K * 16; i += 256) {
+    const int k = i >> 4, c = i & 15;
+    const int bytes = c0 + c < d.ncols ? 8 : 0;
+    cp_async_zfill(tl + c * KS + k, bytes ? src + (long long)k * d.ld + c : src, 0, bytes);
+  }
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+  __syncthreads();
+  const int wc = tid >> 4, lk = tid & 15;       // column, lane within the column's 16 threads
+  const float2* colp = tl + wc * KS;
+  float m = 0.f;
+  for (int k = lk; k < K; k += 16) m = fmaxf(m, fabsf(colp[k].x));
+  red[wc][lk] = m;
+  __syncthreads();
+  if (tid < 16) {
+    float mm = 0.f;
+    for (int i = 0; i < 16; ++i) mm = fmaxf(mm, red[tid][i]);
+    const int e = row_exponent_f(mm);
+    sexp[tid] = e;
+    if (c0 + tid < d.ncols) d.exps[c0 + tid] = e;
+  }
+  __syncthreads();
+  if (c0 + wc >= d.ncols) return;
+  // four consecutive k per thread, stored as one 8-byte word per slice: the 16
+  // threads of a column write 128 contiguous bytes per slice
+  __nv_bfloat16* dst = d.dst + (long long)(c0 + wc) * d.ldK;
+  const int e = sexp[wc];
+  for (int k0 = lk * 4; k0 < K; k0 += 64) {
+    if (k0 + 4 <= K) {
+      float th[4], tl4[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        th[u] = ldexpf(colp[k0 + u].x, 8 - e);
+        tl4[u] = ldexpf(colp[k0 + u].y, 8 - e);
+      }
+      for (int i = 0; i < d.ns; ++i) {
+        __nv_bfloat16 o[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const float S = rintf(th[u]);
+          float sh, sl;
+          two_sum_rn(__fsub_rn(th[u], S), tl4[u], sh, sl);
+          o[u] = __float2bfloat16_rn(ldexpf(S, -8 * (i + 1)));
+          th[u] = __fmul_rn(sh, 256.f);
+          tl4[u] = __fmul_rn(sl, 256.f);
+        }
+        uint2 w;
+        w.x = (unsigned)__bfloat16_as_ushort(o[0]) | ((unsigned)__bfloat16_as_ushort(o[1]) << 16);
+        w.y = (unsigned)__bfloat16_as_ushort(o[2]) | ((unsigned)__bfloat16_as_ushort(o[3]) << 16);
+        *reinterpret_cast<uint2*>(dst + i * d.slice_stride + k0) = w;
+      }
+    } else {
+      for (int k = k0; k < K; ++k) slice_df(colp[k].x, colp[k].y, e, d.ns, dst + k, d.slice_stride);
+    }
   }
 }
 
@@ -230,13 +311,6 @@ __device__ __forceinline__ void df_fma_fused(float vh, float vl, float xh, float
 // nonzero count so the threads of a warp run loops of similar length.
 constexpr int SPMM_SMEM_BYTES = 112 * 1024;
 constexpr int SPMM_THREADS = 256;
-__device__ __forceinline__ void cp_async_zfill(void* dst, const void* src, int cp_bytes16, int src_bytes) {
-  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-  if (cp_bytes16)
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(src_bytes) : "memory");
-  else
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src), "r"(src_bytes) : "memory");
-}
 template <int BW, int TPR>
 __global__ void __launch_bounds__(SPMM_THREADS, 2) spmm_df_smem_kernel(const SpmmDfDesc* __restrict__ descs,
                                                                     const long long* __restrict__ prefix, int nprob) {
@@ -324,9 +398,18 @@ int launch_slice_rows(const SliceRowsDesc* d, const long long* prefix, int n, lo
   slice_rows_kernel<<<(unsigned)((rows + 7) / 8), 256, 0, (cudaStream_t)stream>>>(d, prefix, n, rows);
   return (int)cudaGetLastError();
 }
-int launch_slice_cols(const SliceColsDesc* d, const long long* prefix, int n, long long blocks, void* stream) {
+int launch_slice_cols(const SliceColsDesc* d, const long long* prefix, int n, long long blocks, int max_k,
+                      void* stream) {
   if (blocks <= 0) return 0;
-  slice_cols_kernel<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(d, prefix, n);
+  cudaStream_t st = (cudaStream_t)stream;
+  if (max_k > 1024) {
+    slice_cols_global_kernel<<<(unsigned)blocks, 256, 0, st>>>(d, prefix, n);
+    return (int)cudaGetLastError();
+  }
+  const cudaError_t e =
+      cudaFuncSetAttribute(slice_cols_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SLICE_COLS_SMEM_MAX);
+  if (e != cudaSuccess) return (int)e;
+  slice_cols_kernel<<<(unsigned)blocks, 256, (size_t)16 * (max_k + 1) * sizeof(float2), st>>>(d, prefix, n);
   return (int)cudaGetLastError();
 }
 int launch_slice_sites(const SliceSiteDesc* d, const long long* prefix, int n, long long rows, void* stream) {
