@@ -161,6 +161,13 @@ struct tnqe_ctx {
   DBuf con_ws, con_desc, con_out;
   DBuf tc_ws, tc_desc, tc_err;
   DBuf oz_ws, oz_desc;
+  // the contraction of the unrotated (diagonal) pairs runs on a second stream,
+  // beside the rotation kernel, with its own workspace
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  DBuf oz_ws_side, oz_desc_side, split_out, split_idx;
+  bool no_events = false;                  // profiling events off (work on the side stream)
+  bool err_preset = false;                 // the pipeline error word was cleared before the fork
   DBuf solve_buf;                          // tnqe_solve / tnqe_dependence, sized once for M = 32
   // graph capture / replay of whole matrix-element calls
   bool capturing = false;
@@ -216,6 +223,7 @@ void upload(tnqe_ctx* c, void* dst, const void* src, size_t n) {
 // Event on the context stream; while capturing, an event-record node of the graph
 // (a plain record inside a capture only orders work and is not replayed).
 void record_event(tnqe_ctx* c, cudaEvent_t e) {
+  if (c->no_events) return;
   if (c->capturing) CK(cudaEventRecordWithFlags(e, c->stream, cudaEventRecordExternal));
   else CK(cudaEventRecord(e, c->stream));
 }
@@ -447,6 +455,7 @@ void site_events(tnqe_ctx* c, FinishInfo& fi, bool last, const std::vector<std::
   if (c->capturing) throw Error(TNQE_ERR_STATE, "a captured call must fit one workspace wave");
   fi.single_wave = false;
   CK(cudaStreamSynchronize(c->stream));
+  if (c->no_events) return;
   for (const auto& r : reads) {
     float ms = 0.f;
     CK(cudaEventElapsedTime(&ms, c->pev[r[0]], c->pev[r[1]]));
@@ -699,7 +708,7 @@ void run_contractions_tc(tnqe_ctx* c, const std::vector<std::pair<int, int>>& pa
   CK(cudaMemGetInfo(&freeb, &totalb));
   const double budget = 0.6 * (double)(freeb + c->tc_ws.cap);
   c->tc_err.ensure(256);
-  CK(cudaMemsetAsync(c->tc_err.p, 0, sizeof(int), c->stream));
+  if (!c->err_preset) CK(cudaMemsetAsync(c->tc_err.p, 0, sizeof(int), c->stream));
   size_t p0 = 0;
   while (p0 < (size_t)np) {
     size_t p1 = p0;
@@ -949,7 +958,7 @@ void run_contractions_oz(tnqe_ctx* c, const std::vector<std::pair<int, int>>& pa
   CK(cudaMemGetInfo(&freeb, &totalb));
   const double budget = 0.6 * (double)(freeb + c->oz_ws.cap);
   c->tc_err.ensure(256);
-  CK(cudaMemsetAsync(c->tc_err.p, 0, sizeof(int), c->stream));
+  if (!c->err_preset) CK(cudaMemsetAsync(c->tc_err.p, 0, sizeof(int), c->stream));
   int* derr = c->tc_err.as<int>();
   size_t p0 = 0;
   while (p0 < (size_t)np) {
@@ -1186,18 +1195,86 @@ void run_contractions_oz(tnqe_ctx* c, const std::vector<std::pair<int, int>>& pa
 // Everything the call puts on the stream, with no host synchronisation when the
 // contraction workspace fits one wave: rotations write capacity-padded states,
 // so the contraction is planned from the capacities alone.
+// The contraction of the pairs (i, i), which need no rotation, on the side
+// stream: stream, workspace and descriptor buffers are swapped for the call and
+// profiling events are off.
+struct SideScope {
+  tnqe_ctx* c;
+  explicit SideScope(tnqe_ctx* cc) : c(cc) { swap(); }
+  ~SideScope() { swap(); }
+  void swap() {
+    std::swap(c->stream, c->side);
+    std::swap(c->oz_ws, c->oz_ws_side);
+    std::swap(c->oz_desc, c->oz_desc_side);
+    c->no_events = !c->no_events;
+  }
+};
+
 void enqueue_matrix_elements(tnqe_ctx* c, const std::vector<std::pair<int, int>>& pl, double* dH, double* dS,
                              FinishInfo& fi) {
   const int npairs = (int)pl.size();
   c->launches = 0;
   for (double& x : c->prof) x = 0.0;
+  struct PresetReset {
+    tnqe_ctx* c;
+    ~PresetReset() { c->err_preset = false; }
+  } preset_reset{c};
+  // Pairs (i, i) need no rotation.  With the sliced path their contraction runs
+  // on a second stream while the rotation kernel, which leaves SMs free (one
+  // CTA per rotated pair), runs on the first; results are scattered to the
+  // caller's order at the end.
+  std::vector<int> di, ri;
+  for (int p = 0; p < npairs; ++p) (pl[p].first == pl[p].second ? di : ri).push_back(p);
+  const bool split = c->opt.precision >= TNQE_PREC_BF16X3 && !di.empty() && !ri.empty();
+  std::vector<std::pair<int, int>> pr;
+  double *oH = dH, *oS = dS;
+  if (split) {
+    if (!c->side) {
+      int lo = 0, hi = 0;
+      CK(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+      CK(cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, lo));
+      CK(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
+      CK(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
+    }
+    c->split_out.ensure(sizeof(double) * 2 * npairs);
+    c->split_idx.ensure(sizeof(int) * npairs);
+    oH = c->split_out.as<double>();
+    oS = oH + npairs;
+    std::vector<int> order(di);
+    order.insert(order.end(), ri.begin(), ri.end());
+    upload(c, c->split_idx.p, order.data(), sizeof(int) * npairs);
+    c->tc_err.ensure(256);
+    CK(cudaMemsetAsync(c->tc_err.p, 0, sizeof(int), c->stream));
+    c->err_preset = true;
+    CK(cudaEventRecord(c->ev_fork, c->stream));
+    CK(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
+    {
+      std::vector<std::pair<int, int>> pd;
+      std::vector<KetView> kd;
+      for (int p : di) {
+        pd.push_back(pl[p]);
+        const DevMps& mi = *c->mps[pl[p].first];
+        kd.push_back(KetView{mi.d_t, mi.off, mi.dims});
+      }
+      FinishInfo fs;
+      SideScope scope(c);
+      run_contractions_oz(c, pd, kd, oH, oS, fs);
+      if (!fs.single_wave) fi.single_wave = false;
+    }
+    CK(cudaEventRecord(c->ev_join, c->side));
+    for (int p : ri) pr.push_back(pl[p]);
+  }
+  const std::vector<std::pair<int, int>>& pm = split ? pr : pl;
+  const int nm = (int)pm.size();
+  double* mH = split ? oH + di.size() : dH;
+  double* mS = split ? oS + di.size() : dS;
   record_event(c, c->ev[0]);
   RotBatch rb;
-  run_rotations(c, pl, rb, 1);
+  run_rotations(c, pm, rb, 1);
   record_event(c, c->ev[1]);
-  std::vector<KetView> kets(npairs);
-  for (int p = 0; p < npairs; ++p) {
-    const DevMps& mi = *c->mps[pl[p].first];
+  std::vector<KetView> kets(nm);
+  for (int p = 0; p < nm; ++p) {
+    const DevMps& mi = *c->mps[pm[p].first];
     kets[p].base = mi.d_t;
     kets[p].off = mi.off;
     kets[p].dims = mi.dims;
@@ -1209,10 +1286,15 @@ void enqueue_matrix_elements(tnqe_ctx* c, const std::vector<std::pair<int, int>>
     kv.dims = rb.cap[k];
   }
   record_event(c, c->ev[2]);
-  if (c->opt.precision == TNQE_PREC_TF32X3) run_contractions_tc(c, pl, kets, dH, dS, fi);
-  else if (c->opt.precision >= TNQE_PREC_BF16X3) run_contractions_oz(c, pl, kets, dH, dS, fi);
-  else run_contractions(c, pl, kets, dH, dS, fi);
+  if (c->opt.precision == TNQE_PREC_TF32X3) run_contractions_tc(c, pm, kets, mH, mS, fi);
+  else if (c->opt.precision >= TNQE_PREC_BF16X3) run_contractions_oz(c, pm, kets, mH, mS, fi);
+  else run_contractions(c, pm, kets, mH, mS, fi);
   record_event(c, c->ev[3]);
+  if (split) {
+    CK(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
+    CKL(launch_scatter_pairs(oH, oS, c->split_idx.as<int>(), npairs, dH, dS, c->stream));
+    c->launches += 1;
+  }
   fi.nrot = (int)rb.pair_idx.size();
   if (fi.nrot) {
     fi.rot_small = c->rot_small.as<unsigned char>();
@@ -1300,7 +1382,8 @@ void capture_matrix_elements(tnqe_ctx* c, const std::vector<std::pair<int, int>>
     cudaGraph_t g = nullptr;
     const cudaError_t e = cudaStreamEndCapture(c->stream, &g);
     ok = ok && e == cudaSuccess && g != nullptr && g_alloc_epoch.load() == epoch0;
-    if (ok) ok = cudaGraphInstantiate(&ge->exec, g, 0) == cudaSuccess;
+    // per-node priorities: the rotation kernel keeps its launch priority in the replays
+    if (ok) ok = cudaGraphInstantiate(&ge->exec, g, cudaGraphInstantiateFlagUseNodePriority) == cudaSuccess;
     if (g) cudaGraphDestroy(g);
   }
   cudaGetLastError();   // a failed capture leaves no sticky error behind
@@ -1859,6 +1942,13 @@ void tnqe_destroy(tnqe_ctx* c) {
   c->tc_err.release();
   c->oz_ws.release();
   c->oz_desc.release();
+  c->oz_ws_side.release();
+  c->oz_desc_side.release();
+  c->split_out.release();
+  c->split_idx.release();
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_join) cudaEventDestroy(c->ev_join);
+  if (c->side) cudaStreamDestroy(c->side);
   c->solve_buf.release();
   c->graphs.clear();
   for (auto& e : c->ev)

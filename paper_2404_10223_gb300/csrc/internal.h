@@ -181,6 +181,8 @@ int spmm_df_smem_width(int max_ncols_x);   // bw in {8, 4, 2, 1}, 0 if the X sla
 int launch_spmm_df_smem(const SpmmDfDesc* d, const long long* prefix, int n, long long blocks, int bw,
                         int max_ncols_x, void* stream);
 int launch_unit_env(float2* const* env, int n, void* stream);
+int launch_scatter_pairs(const double* h, const double* s, const int* idx, int n, double* H, double* S,
+                         void* stream);
 int launch_unit_env_f64(double* const* env, int n, void* stream);
 int launch_unit_env_f32(float* const* env, int n, void* stream);
 int launch_extract_df(const float2* const* fin, int npairs, double* H, double* S, void* stream);

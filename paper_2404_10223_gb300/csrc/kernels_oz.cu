@@ -73,6 +73,31 @@ __device__ __forceinline__ void slice_df(float hi, float lo, int e, int ns, __nv
     tl = __fmul_rn(sl, 256.f);
   }
 }
+// slice_df of four consecutive values, each slice stored as one 8-byte word (out 8-byte aligned)
+__device__ __forceinline__ void slice_df4(const float2* x, int e, int ns, __nv_bfloat16* out, long long stride) {
+  float th[4], tl[4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    th[u] = ldexpf(x[u].x, 8 - e);
+    tl[u] = ldexpf(x[u].y, 8 - e);
+  }
+  for (int i = 0; i < ns; ++i) {
+    unsigned short o[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const float S = rintf(th[u]);
+      float sh, sl;
+      two_sum_rn(__fsub_rn(th[u], S), tl[u], sh, sl);
+      o[u] = __bfloat16_as_ushort(__float2bfloat16_rn(ldexpf(S, -8 * (i + 1))));
+      th[u] = __fmul_rn(sh, 256.f);
+      tl[u] = __fmul_rn(sl, 256.f);
+    }
+    uint2 w;
+    w.x = (unsigned)o[0] | ((unsigned)o[1] << 16);
+    w.y = (unsigned)o[2] | ((unsigned)o[3] << 16);
+    *reinterpret_cast<uint2*>(out + i * stride) = w;
+  }
+}
 __device__ __forceinline__ void slice_d(double x, int e, int ns, __nv_bfloat16* out, long long stride) {
   double t = ldexp(x, 8 - e);
   for (int i = 0; i < ns; ++i) {
@@ -93,13 +118,41 @@ __global__ void __launch_bounds__(256) slice_rows_kernel(const SliceRowsDesc* __
   const SliceRowsDesc& d = descs[p];
   const long long r = task - prefix[p];
   const float2* src = d.src + r * d.ld;
+  __nv_bfloat16* dst = d.dst + r * d.ldK;
+  if (d.K <= 256) {
+    // the row sits in registers (four consecutive values per lane and 128-value chunk):
+    // one read, and each slice leaves as 8-byte words
+    float2 v[8];
+    float m = 0.f;
+#pragma unroll
+    for (int j = 0; j < 2; ++j)
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int k = 128 * j + 4 * lane + u;
+        v[4 * j + u] = k < d.K ? src[k] : make_float2(0.f, 0.f);
+        m = fmaxf(m, fabsf(v[4 * j + u].x));
+      }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    const int e = row_exponent_f(m);
+    if (lane == 0) d.exps[r] = e;
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int k0 = 128 * j + 4 * lane;
+      if (k0 + 4 <= d.K) {
+        slice_df4(v + 4 * j, e, d.ns, dst + k0, d.slice_stride);
+      } else {
+        for (int u = 0; u < 4 && k0 + u < d.K; ++u) slice_df(v[4 * j + u].x, v[4 * j + u].y, e, d.ns, dst + k0 + u, d.slice_stride);
+      }
+    }
+    return;
+  }
   float m = 0.f;
   for (int k = lane; k < d.K; k += 32) m = fmaxf(m, fabsf(src[k].x));
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
   const int e = row_exponent_f(m);
   if (lane == 0) d.exps[r] = e;
-  __nv_bfloat16* dst = d.dst + r * d.ldK;
   for (int k = lane; k < d.K; k += 32) {
     const float2 x = src[k];
     slice_df(x.x, x.y, e, d.ns, dst + k, d.slice_stride);
@@ -195,28 +248,7 @@ __global__ void __launch_bounds__(256) slice_cols_kernel(const SliceColsDesc* __
   const int e = sexp[wc];
   for (int k0 = lk * 4; k0 < K; k0 += 64) {
     if (k0 + 4 <= K) {
-      float th[4], tl4[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        th[u] = ldexpf(colp[k0 + u].x, 8 - e);
-        tl4[u] = ldexpf(colp[k0 + u].y, 8 - e);
-      }
-      for (int i = 0; i < d.ns; ++i) {
-        __nv_bfloat16 o[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const float S = rintf(th[u]);
-          float sh, sl;
-          two_sum_rn(__fsub_rn(th[u], S), tl4[u], sh, sl);
-          o[u] = __float2bfloat16_rn(ldexpf(S, -8 * (i + 1)));
-          th[u] = __fmul_rn(sh, 256.f);
-          tl4[u] = __fmul_rn(sl, 256.f);
-        }
-        uint2 w;
-        w.x = (unsigned)__bfloat16_as_ushort(o[0]) | ((unsigned)__bfloat16_as_ushort(o[1]) << 16);
-        w.y = (unsigned)__bfloat16_as_ushort(o[2]) | ((unsigned)__bfloat16_as_ushort(o[3]) << 16);
-        *reinterpret_cast<uint2*>(dst + i * d.slice_stride + k0) = w;
-      }
+      slice_df4(colp + k0, e, d.ns, dst + k0, d.slice_stride);
     } else {
       for (int k = k0; k < K; ++k) slice_df(colp[k].x, colp[k].y, e, d.ns, dst + k, d.slice_stride);
     }
@@ -391,8 +423,23 @@ __global__ void extract_df_kernel(const float2* const* __restrict__ fin, int npa
   H[p] = (double)h.x + (double)h.y;
 }
 
+// H[idx[p]] = h[p], S[idx[p]] = s[p]
+__global__ void scatter_pairs_kernel(const double* __restrict__ h, const double* __restrict__ s,
+                                     const int* __restrict__ idx, int n, double* H, double* S) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  H[idx[p]] = h[p];
+  S[idx[p]] = s[p];
+}
+
 }  // namespace
 
+int launch_scatter_pairs(const double* h, const double* s, const int* idx, int n, double* H, double* S,
+                         void* stream) {
+  if (n <= 0) return 0;
+  scatter_pairs_kernel<<<(n + 127) / 128, 128, 0, (cudaStream_t)stream>>>(h, s, idx, n, H, S);
+  return (int)cudaGetLastError();
+}
 int launch_slice_rows(const SliceRowsDesc* d, const long long* prefix, int n, long long rows, void* stream) {
   if (rows <= 0) return 0;
   slice_rows_kernel<<<(unsigned)((rows + 7) / 8), 256, 0, (cudaStream_t)stream>>>(d, prefix, n, rows);

@@ -1011,7 +1011,21 @@ __global__ void __launch_bounds__(RT_THREADS) rotate_pairs_kernel(const RotDesc*
 int launch_rotate(const RotDesc* d_descs, int npairs, int smem_bytes, void* stream) {
   if (npairs <= 0) return 0;
   (void)smem_bytes;
-  rotate_pairs_kernel<<<npairs, RT_THREADS, 0, (cudaStream_t)stream>>>(d_descs);
+  // The highest launch priority: each CTA needs a whole SM's register file, so
+  // its CTAs must take their SMs before the kernels of a concurrent stream do.
+  int lo = 0, hi = 0;
+  cudaDeviceGetStreamPriorityRange(&lo, &hi);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)npairs);
+  cfg.blockDim = dim3(RT_THREADS);
+  cfg.stream = (cudaStream_t)stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributePriority;
+  attr[0].val.priority = hi;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  const cudaError_t e = cudaLaunchKernelEx(&cfg, rotate_pairs_kernel, d_descs);
+  if (e != cudaSuccess) return (int)e;
   return (int)cudaGetLastError();
 }
 
