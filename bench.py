@@ -277,7 +277,7 @@ def run_native(args):
     # captured case to this launch by the units it processes; None where no capture of the
     # current kernel exists for this workload.
     n_rot = sum(1 for i, j in pairs if i != j)
-    traffic_table = {("n14_chi128", "rotate_pairs_kernel"): 587.0e6 / 2 * n_rot}   # rotate_pairs_n14_small.md
+    traffic_table = {}     # refilled from a capture of the current kernels
     traffic = traffic_table.get((w.name, top))
     t_ms, work, bound, peak, unit = kern[top]
     achieved = (work / (t_ms / 1e3)) / (1e12 if unit == "TFLOP/s" else 1e9) if t_ms > 0 else 0.0
@@ -289,7 +289,10 @@ def run_native(args):
                                         "measured bf16 burst; achieved counts every issued slice product"),
                              "hbm": f"hbm_gbs ({peak_src})"}[bound]),
             "ms_per_step": t_ms, "work_per_step": work,
-            "breakdown_ms": {k: v[0] for k, v in kern.items()}}
+            "breakdown_ms": {k: v[0] for k, v in kern.items()},
+            "breakdown_scope": ("kernels of the main stream; with the sliced path the (i, i) pairs, which "
+                                "need no rotation, contract on a second stream beside the rotation kernel "
+                                "and are not in the breakdown")}
     # the plain FP64 form on the same workload, and |dE| of this precision against it
     Hh = Hd.cpu().numpy().copy()
     Sh = Sd.cpu().numpy().copy()

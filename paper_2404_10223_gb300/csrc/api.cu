@@ -1247,21 +1247,6 @@ void enqueue_matrix_elements(tnqe_ctx* c, const std::vector<std::pair<int, int>>
     CK(cudaMemsetAsync(c->tc_err.p, 0, sizeof(int), c->stream));
     c->err_preset = true;
     CK(cudaEventRecord(c->ev_fork, c->stream));
-    CK(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
-    {
-      std::vector<std::pair<int, int>> pd;
-      std::vector<KetView> kd;
-      for (int p : di) {
-        pd.push_back(pl[p]);
-        const DevMps& mi = *c->mps[pl[p].first];
-        kd.push_back(KetView{mi.d_t, mi.off, mi.dims});
-      }
-      FinishInfo fs;
-      SideScope scope(c);
-      run_contractions_oz(c, pd, kd, oH, oS, fs);
-      if (!fs.single_wave) fi.single_wave = false;
-    }
-    CK(cudaEventRecord(c->ev_join, c->side));
     for (int p : ri) pr.push_back(pl[p]);
   }
   const std::vector<std::pair<int, int>>& pm = split ? pr : pl;
@@ -1272,6 +1257,24 @@ void enqueue_matrix_elements(tnqe_ctx* c, const std::vector<std::pair<int, int>>
   RotBatch rb;
   run_rotations(c, pm, rb, 1);
   record_event(c, c->ev[1]);
+  if (split) {
+    // submitted after the rotation kernel, so that its CTAs take their SMs first
+    CK(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
+    std::vector<std::pair<int, int>> pd;
+    std::vector<KetView> kd;
+    for (int p : di) {
+      pd.push_back(pl[p]);
+      const DevMps& mi = *c->mps[pl[p].first];
+      kd.push_back(KetView{mi.d_t, mi.off, mi.dims});
+    }
+    {
+      FinishInfo fs;
+      SideScope scope(c);
+      run_contractions_oz(c, pd, kd, oH, oS, fs);
+      if (!fs.single_wave) fi.single_wave = false;
+    }
+    CK(cudaEventRecord(c->ev_join, c->side));
+  }
   std::vector<KetView> kets(nm);
   for (int p = 0; p < nm; ++p) {
     const DevMps& mi = *c->mps[pm[p].first];
