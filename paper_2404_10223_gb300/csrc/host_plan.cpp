@@ -6,7 +6,8 @@
 #include <cmath>
 #include <cstring>
 #include <stdexcept>
-#include <unordered_map>
+#include <exception>
+#include <thread>
 
 #include "internal.h"
 
@@ -206,34 +207,85 @@ int key_nops(uint64_t k) { return (int)((k >> 2) & 3); }
 
 struct Block { Mat4 M; };
 
-}  // namespace
+// Open-addressing hash map uint64 -> int (linear probing, power-of-two table)
+// for the MPO builder, which looks up several keys per Hamiltonian term
+// (O(N^4) terms).  No key used here has all bits set, so that value marks an
+// empty slot.
+class FlatMap {
+ public:
+  explicit FlatMap(size_t expect = 64) { rehash(std::max<size_t>(64, expect * 2)); }
+  int* find(uint64_t k) {
+    size_t i = slot(k);
+    while (true) {
+      if (keys_[i] == k) return &vals_[i];
+      if (keys_[i] == EMPTY) return nullptr;
+      i = (i + 1) & mask_;
+    }
+  }
+  void insert(uint64_t k, int v) {           // k must be absent
+    if (2 * (n_ + 1) > keys_.size()) rehash(keys_.size() * 2);
+    size_t i = slot(k);
+    while (keys_[i] != EMPTY) i = (i + 1) & mask_;
+    keys_[i] = k;
+    vals_[i] = v;
+    ++n_;
+  }
+  bool contains(uint64_t k) { return find(k) != nullptr; }
 
-Mpo build_mpo(const double* h1, const double* eri, int N) {
-  const int half = N / 2;
-  const Mat4 I4 = mat_identity(), P4 = mat_parity();
-  Mat4 lad[2][2];
-  for (int sp = 0; sp < 2; ++sp)
-    for (int cr = 0; cr < 2; ++cr) lad[sp][cr] = mat_ladder(sp, cr != 0);
+ private:
+  static constexpr uint64_t EMPTY = ~0ull;
+  size_t slot(uint64_t k) const {
+    k ^= k >> 33;
+    k *= 0xff51afd7ed558ccdull;
+    k ^= k >> 33;
+    return (size_t)k & mask_;
+  }
+  void rehash(size_t cap) {
+    std::vector<uint64_t> ok;
+    std::vector<int> ov;
+    ok.swap(keys_);
+    ov.swap(vals_);
+    keys_.assign(cap, EMPTY);
+    vals_.assign(cap, 0);
+    mask_ = cap - 1;
+    n_ = 0;
+    for (size_t i = 0; i < ok.size(); ++i)
+      if (ok[i] != EMPTY) insert(ok[i], ov[i]);
+  }
+  std::vector<uint64_t> keys_;
+  std::vector<int> vals_;
+  size_t mask_ = 0, n_ = 0;
+};
 
-  std::unordered_map<uint64_t, int> key_id;
+// Operator-string bookkeeping of a share of the Hamiltonian terms: channel
+// keys seen (with the first and last bond each is alive on) and, per site, the
+// 4 x 4 blocks between channel keys.  Blocks that complete a term (from the
+// identity or a left-named channel into a right-named or the full one) sum the
+// coefficients; the others are fixed by their keys.
+struct TermSink {
+  int N, half;
+  const std::vector<Mat4>* lprod;
+  FlatMap key_id{4096};
   std::vector<uint64_t> keys;
   std::vector<int> kstart, kend;
-  auto kid = [&](uint64_t k) {
-    auto it = key_id.find(k);
-    if (it != key_id.end()) return it->second;
+  std::vector<FlatMap> site_blocks;
+  std::vector<std::vector<std::pair<uint64_t, Mat4>>> blocks;   // (kin_id << 32 | kout_id, M)
+
+  TermSink(int n_sites, const std::vector<Mat4>* lp)
+      : N(n_sites), half(n_sites / 2), lprod(lp), site_blocks(n_sites, FlatMap(1024)), blocks(n_sites) {
+    kid(KEY_I);
+    kid(KEY_F);
+  }
+  int kid(uint64_t k) {
+    if (int* f = key_id.find(k)) return *f;
     int id = (int)keys.size();
-    key_id.emplace(k, id);
+    key_id.insert(k, id);
     keys.push_back(k);
     kstart.push_back(1 << 30);
     kend.push_back(-1);
     return id;
-  };
-  kid(KEY_I);
-  kid(KEY_F);
-  std::vector<std::unordered_map<uint64_t, int>> site_blocks(N);
-  std::vector<std::vector<std::pair<uint64_t, Mat4>>> blocks(N);   // (kin_id << 32 | kout_id, M)
-
-  auto key_at = [&](const int* codes, const int* sites, int n, int b) -> uint64_t {
+  }
+  uint64_t key_at(const int* codes, const int* sites, int n, int b) const {
     int k = 0;
     while (k < n && sites[k] < b) ++k;
     if (k == 0) return KEY_I;
@@ -241,9 +293,8 @@ Mpo build_mpo(const double* h1, const double* eri, int N) {
     if (k == 1) return make_key(2, codes, 1);
     if (k == 3) return make_key(3, codes + 3, 1);
     return (b <= half) ? make_key(2, codes, 2) : make_key(3, codes + 2, 2);
-  };
-
-  auto add_term = [&](double coef, int n, const int* pos_in, const int* cre_in) {
+  }
+  void add_term(double coef, int n, const int* pos_in, const int* cre_in) {
     if (coef == 0.0) return;
     // identical operators (same position and kind) make the term vanish
     for (int i = 0; i < n; ++i)
@@ -279,56 +330,168 @@ Mpo build_mpo(const double* h1, const double* eri, int N) {
     }
     for (int e = 0; e < nev; ++e) {
       const int t = ev[e];
-      Mat4 L = I4;
-      int after = 0;
+      int after = 0, cnt = 0, combo = 0;
       for (int i = 0; i < n; ++i) {
-        if (sites[i] == t) L = mat_mul(L, lad[pos[i] & 1][cre[i]]);
+        if (sites[i] == t) {
+          combo = combo * 4 + (pos[i] & 1) * 2 + cre[i];
+          ++cnt;
+        }
         if (sites[i] > t) ++after;
       }
-      Mat4 M = (after & 1) ? mat_mul(L, P4) : L;
+      Mat4 M = lprod[cnt][combo];
+      if (after & 1)                             // times the parity string: columns 1, 2 change sign
+        for (int k = 0; k < 4; ++k) {
+          M.m[k * 4 + 1] = -M.m[k * 4 + 1];
+          M.m[k * 4 + 2] = -M.m[k * 4 + 2];
+        }
       uint64_t kin = key_at(codes, sites, n, t), kout = key_at(codes, sites, n, t + 1);
       int iin = kid(kin), iout = kid(kout);
       kend[iin] = std::max(kend[iin], t);
       kstart[iout] = std::min(kstart[iout], t + 1);
       const bool trans = (key_type(kin) == 0 || key_type(kin) == 2) && (key_type(kout) == 1 || key_type(kout) == 3);
       const uint64_t pk = ((uint64_t)iin << 32) | (uint64_t)iout;
-      auto it = site_blocks[t].find(pk);
+      int* it = site_blocks[t].find(pk);
       if (trans) {
         const double f = coef * sgn;
-        if (it == site_blocks[t].end()) {
+        if (!it) {
           Mat4 S{};
           for (int q = 0; q < 16; ++q) S.m[q] = f * M.m[q];
-          site_blocks[t].emplace(pk, (int)blocks[t].size());
+          site_blocks[t].insert(pk, (int)blocks[t].size());
           blocks[t].push_back({pk, S});
         } else {
-          Mat4& S = blocks[t][it->second].second;
+          Mat4& S = blocks[t][*it].second;
           for (int q = 0; q < 16; ++q) S.m[q] += f * M.m[q];
         }
-      } else if (it == site_blocks[t].end()) {
-        site_blocks[t].emplace(pk, (int)blocks[t].size());
+      } else if (!it) {
+        site_blocks[t].insert(pk, (int)blocks[t].size());
         blocks[t].push_back({pk, M});
       }
     }
-  };
-
-  for (int p = 0; p < N; ++p)
-    for (int q = 0; q < N; ++q)
-      for (int s = 0; s < 2; ++s) {
-        int pos[2] = {2 * p + s, 2 * q + s}, cre[2] = {1, 0};
-        add_term(h1[(size_t)p * N + q], 2, pos, cre);
+  }
+  // channel keys of another sink: their ids here, alive ranges widened
+  std::vector<int> merge_keys(const TermSink& o) {
+    std::vector<int> gid(o.keys.size());
+    for (size_t id = 0; id < o.keys.size(); ++id) {
+      const int g = kid(o.keys[id]);
+      gid[id] = g;
+      kstart[g] = std::min(kstart[g], o.kstart[id]);
+      kend[g] = std::max(kend[g], o.kend[id]);
+    }
+    return gid;
+  }
+  // site t's blocks of another sink, in its order (the sums of completing blocks add up)
+  void merge_site(const TermSink& o, const std::vector<int>& gid, int t) {
+    for (const auto& bl : o.blocks[t]) {
+      const int iin = gid[bl.first >> 32], iout = gid[bl.first & 0xffffffffu];
+      const uint64_t pk = ((uint64_t)iin << 32) | (uint64_t)iout;
+      int* it = site_blocks[t].find(pk);
+      if (!it) {
+        site_blocks[t].insert(pk, (int)blocks[t].size());
+        blocks[t].push_back({pk, bl.second});
+      } else {
+        const uint64_t kin = keys[iin], kout = keys[iout];
+        const bool trans = (key_type(kin) == 0 || key_type(kin) == 2) && (key_type(kout) == 1 || key_type(kout) == 3);
+        if (trans) {
+          Mat4& S = blocks[t][*it].second;
+          for (int q = 0; q < 16; ++q) S.m[q] += bl.second.m[q];
+        }
       }
-  for (int p = 0; p < N; ++p)
-    for (int q = 0; q < N; ++q)
-      for (int r = 0; r < N; ++r)
-        for (int ss = 0; ss < N; ++ss) {
-          const double v = eri[(((size_t)p * N + q) * N + r) * N + ss];
-          if (v == 0.0) continue;
+    }
+  }
+};
+
+// Fixed number of term shares: the MPO comes out the same on every machine.
+constexpr int MPO_THREADS = 8;
+
+// f(i) for i in [0, n) on MPO_THREADS threads (strided); the first exception is rethrown
+template <class F>
+void parallel_for(int n, F f) {
+  const int nt = std::min(MPO_THREADS, std::max(1, n));
+  std::vector<std::exception_ptr> errs(nt);
+  auto run = [&](int w) {
+    try {
+      for (int i = w; i < n; i += nt) f(i);
+    } catch (...) {
+      errs[w] = std::current_exception();
+    }
+  };
+  std::vector<std::thread> th;
+  for (int w = 1; w < nt; ++w) th.emplace_back(run, w);
+  run(0);
+  for (auto& x : th) x.join();
+  for (auto& e : errs)
+    if (e) std::rethrow_exception(e);
+}
+
+}  // namespace
+
+Mpo build_mpo(const double* h1, const double* eri, int N) {
+  const int half = N / 2;
+  const Mat4 I4 = mat_identity(), P4 = mat_parity();
+  Mat4 lad[2][2];
+  for (int sp = 0; sp < 2; ++sp)
+    for (int cr = 0; cr < 2; ++cr) lad[sp][cr] = mat_ladder(sp, cr != 0);
+  // products of up to four ladder operators on one site, indexed by their
+  // count and (spin, create) codes in order: lprod[cnt][combo]
+  std::vector<Mat4> lprod_all[5];
+  lprod_all[0].assign(1, I4);
+  for (int cnt = 1; cnt <= 4; ++cnt) {
+    lprod_all[cnt].resize((size_t)1 << (2 * cnt));
+    for (size_t combo = 0; combo < lprod_all[cnt].size(); ++combo) {
+      const int last = (int)(combo & 3);
+      lprod_all[cnt][combo] = mat_mul(lprod_all[cnt - 1][combo >> 2], lad[last >> 1][last & 1]);
+    }
+  }
+  // the terms in MPO_THREADS shares (by the first index of the two-body terms),
+  // each on its own thread, merged in share order
+  const int nsh = std::min(MPO_THREADS, std::max(1, N));
+  std::vector<TermSink> sinks;
+  sinks.reserve(nsh);
+  for (int w = 0; w < nsh; ++w) sinks.emplace_back(N, lprod_all);
+  parallel_for(nsh, [&](int w) {
+    TermSink& S = sinks[w];
+    if (w == 0)
+      for (int p = 0; p < N; ++p)
+        for (int q = 0; q < N; ++q)
+          for (int s = 0; s < 2; ++s) {
+            int pos[2] = {2 * p + s, 2 * q + s}, cre[2] = {1, 0};
+            S.add_term(h1[(size_t)p * N + q], 2, pos, cre);
+          }
+    // (pq|rs) with spins (s, t) and (rs|pq) with (t, s) are the same operator
+    // string with the same sign (the two creators and the two annihilators
+    // swap): one term with the summed coefficient per pair P = (p, q) <= R = (r, s)
+    const size_t NN = (size_t)N * N;
+    for (int p = w; p < N; p += nsh)
+      for (int q = 0; q < N; ++q) {
+        const size_t P = (size_t)p * N + q;
+        for (size_t R = P; R < NN; ++R) {
+          const int r = (int)(R / N), ss = (int)(R % N);
+          const double vpr = eri[P * NN + R], vrp = eri[R * NN + P];
           for (int s = 0; s < 2; ++s)
             for (int t = 0; t < 2; ++t) {
+              double coef;
+              if (R != P) coef = 0.5 * vpr + 0.5 * vrp;
+              else if (s == t) coef = 0.5 * vpr;
+              else if (s < t) coef = vpr;                // (s, t) and (t, s) are one string
+              else continue;
+              if (coef == 0.0) continue;
               int pos[4] = {2 * p + s, 2 * r + t, 2 * ss + t, 2 * q + s}, cre[4] = {1, 1, 0, 0};
-              add_term(0.5 * v, 4, pos, cre);
+              S.add_term(coef, 4, pos, cre);
             }
         }
+      }
+  });
+  TermSink& G = sinks[0];
+  std::vector<std::vector<int>> gids(nsh);
+  for (int w = 1; w < nsh; ++w) gids[w] = G.merge_keys(sinks[w]);
+  parallel_for(N, [&](int t) {
+    for (int w = 1; w < nsh; ++w) G.merge_site(sinks[w], gids[w], t);
+  });
+  std::vector<uint64_t>& keys = G.keys;
+  std::vector<int>& kstart = G.kstart;
+  std::vector<int>& kend = G.kend;
+  std::vector<FlatMap>& site_blocks = G.site_blocks;
+  std::vector<std::vector<std::pair<uint64_t, Mat4>>>& blocks = G.blocks;
   // identity string everywhere (gives the overlap), completed H to the end
   kstart[0] = 0;
   kend[0] = N;
@@ -349,19 +512,19 @@ Mpo build_mpo(const double* h1, const double* eri, int N) {
     for (auto& a : alive) chan_of[b][a.second] = c++;
     mpo.dims[b] = c;
   }
-  // pass-through of every channel alive on both sides of a site
-  for (int t = 0; t < N; ++t)
+  // per site (independent, in parallel): pass-through of every channel alive on
+  // both sides of the site, then the CSR rows
+  mpo.sites.resize(N);
+  parallel_for(N, [&](int t) {
     for (size_t id = 0; id < keys.size(); ++id) {
       if (chan_of[t][id] < 0 || chan_of[t + 1][id] < 0) continue;
       const uint64_t pk = ((uint64_t)id << 32) | (uint64_t)id;
-      if (site_blocks[t].count(pk)) continue;
+      if (site_blocks[t].contains(pk)) continue;
       const int tp = key_type(keys[id]);
       const bool odd = (tp >= 2) && (key_nops(keys[id]) & 1);
-      site_blocks[t].emplace(pk, (int)blocks[t].size());
+      site_blocks[t].insert(pk, (int)blocks[t].size());
       blocks[t].push_back({pk, odd ? P4 : I4});
     }
-  mpo.sites.resize(N);
-  for (int t = 0; t < N; ++t) {
     MpoSite& S = mpo.sites[t];
     S.Din = mpo.dims[t];
     S.Dout = mpo.dims[t + 1];
@@ -386,7 +549,7 @@ Mpo build_mpo(const double* h1, const double* eri, int N) {
         S.val.push_back(e.second);
       }
     }
-  }
+  });
   return mpo;
 }
 
