@@ -86,6 +86,23 @@ typedef struct {
  * graphs on. */
 void tnqe_default_options(tnqe_options* opt);
 
+/* The Hamiltonian MPO the library builds for integrals (h1, eri) (Eq. 1 in
+ * second quantisation, Sec. II A; one per state basis inside tnqe_add_mps),
+ * computed on the host, no GPU needed.  h1: N*N row-major; eri: N^4
+ * row-major chemists' (pq|rs); 1 <= N <= 32.  Site t is a sparse
+ * (4 D_{t+1}) x (4 D_t) matrix in CSR: row k * D_{t+1} + w' (bra local state
+ * k, right channel w'), column w * 4 + k' (left channel w, ket local state
+ * k'); channel 0 of every bond is the identity string, channel 1 of bonds
+ * >= 1 the completed Hamiltonian, so D_0 = 1 and D_N = 2.
+ * Outputs: dims[N + 1] (bond dimensions D_t), nnz[N] (nonzeros per site).
+ * If rowptr, col and val are all non-NULL they receive every site in turn:
+ * rowptr holds sum_t (4 D_{t+1} + 1) entries (site-local offsets), col and
+ * val hold sum_t nnz[t] entries; cap is the capacity of col and val
+ * (TNQE_ERR_ARG if it is too small).  Call once with NULL buffers to size
+ * them.  The result does not depend on the machine (fixed work shares). */
+tnqe_status tnqe_mpo_host(const double* h1, const double* eri, int N, int* dims, long long* nnz, int* rowptr,
+                          int* col, double* val, long long cap);
+
 /* Create a context for N spatial orbitals and (n_alpha, n_beta) electrons.
  * h1: N*N row-major, symmetric.  eri: N^4 row-major (pq|rs).  Both copied.
  * Requires 1 <= N <= 32 and n_alpha, n_beta <= 14.  opt may be NULL.

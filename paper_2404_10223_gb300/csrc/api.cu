@@ -1561,6 +1561,36 @@ void tnqe_default_options(tnqe_options* o) {
   o->use_graphs = 1;
 }
 
+tnqe_status tnqe_mpo_host(const double* h1, const double* eri, int N, int* dims, long long* nnz, int* rowptr,
+                          int* col, double* val, long long cap) {
+  try {
+    if (!h1 || !eri || !dims || !nnz || N < 1 || N > 32) return TNQE_ERR_ARG;
+    const tnqe::Mpo m = tnqe::build_mpo(h1, eri, N);
+    long long total = 0;
+    for (int b = 0; b <= N; ++b) dims[b] = m.dims[b];
+    for (int t = 0; t < N; ++t) {
+      nnz[t] = (long long)m.sites[t].val.size();
+      total += nnz[t];
+    }
+    if (!rowptr || !col || !val) return TNQE_OK;
+    if (cap < total) return TNQE_ERR_ARG;
+    long long ro = 0, eo = 0;
+    for (int t = 0; t < N; ++t) {
+      const tnqe::MpoSite& S = m.sites[t];
+      std::copy(S.rowptr.begin(), S.rowptr.end(), rowptr + ro);
+      std::copy(S.col.begin(), S.col.end(), col + eo);
+      std::copy(S.val.begin(), S.val.end(), val + eo);
+      ro += (long long)S.rowptr.size();
+      eo += (long long)S.val.size();
+    }
+    return TNQE_OK;
+  } catch (const std::bad_alloc&) {
+    return TNQE_ERR_NOMEM;
+  } catch (...) {
+    return TNQE_ERR_STATE;
+  }
+}
+
 tnqe_status tnqe_create(const double* h1, const double* eri, int N, int n_alpha, int n_beta,
                         const tnqe_options* opt, tnqe_ctx** out) {
   if (!out) return TNQE_ERR_ARG;

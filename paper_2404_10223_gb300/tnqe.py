@@ -37,7 +37,7 @@ class tnqe_options(ctypes.Structure):
                 ("cuda_stream", ctypes.c_void_p), ("device", ctypes.c_int), ("use_graphs", ctypes.c_int)]
 
 
-EXPORTED = ["tnqe_default_options", "tnqe_create", "tnqe_add_mps", "tnqe_reset_mps", "tnqe_rotate",
+EXPORTED = ["tnqe_default_options", "tnqe_mpo_host", "tnqe_create", "tnqe_add_mps", "tnqe_reset_mps", "tnqe_rotate",
             "tnqe_get_rotated", "tnqe_matrix_elements", "tnqe_solve", "tnqe_set_precision", "tnqe_last_timing", "tnqe_last_profile", "tnqe_apply_gate_noalloc",
             "tnqe_solve_ex", "tnqe_dependence", "tnqe_autotune", "tnqe_set_tuning", "tnqe_clear_graphs", "tnqe_graph_count", "tnqe_last_error",
             "tnqe_destroy"]
@@ -56,6 +56,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.tnqe_default_options.argtypes = [ctypes.POINTER(tnqe_options)]
     lib.tnqe_default_options.restype = None
     lib.tnqe_create.argtypes = [P, P, I, I, I, ctypes.POINTER(tnqe_options), ctypes.POINTER(P)]
+    lib.tnqe_mpo_host.argtypes = [P, P, I, P, P, P, P, P, LL]
     lib.tnqe_add_mps.argtypes = [P, P, P, P, ctypes.POINTER(I)]
     lib.tnqe_reset_mps.argtypes = [P]
     lib.tnqe_rotate.argtypes = [P, I, I, ctypes.POINTER(D)]
@@ -104,6 +105,32 @@ def tnqe_default_options() -> tnqe_options:
     o = tnqe_options()
     load().tnqe_default_options(ctypes.byref(o))
     return o
+
+
+def tnqe_mpo_host(h1, eri, N: int):
+    """The library's Hamiltonian MPO (host build): (dims, [(rowptr, col, val) per site]).
+
+    Site t is a (4 D_{t+1}) x (4 D_t) CSR matrix, row k * D_{t+1} + w', column w * 4 + k'."""
+    lib = load()
+    h1, eri = _f64(h1), _f64(eri)
+    dims = np.zeros(N + 1, dtype=np.int32)
+    nnz = np.zeros(N, dtype=np.int64)
+    _check(None, lib.tnqe_mpo_host(_ptr(h1), _ptr(eri), N, _ptr(dims), _ptr(nnz), None, None, None, 0))
+    nrp = int(sum(4 * int(dims[t + 1]) + 1 for t in range(N)))
+    tot = int(nnz.sum())
+    rowptr = np.zeros(nrp, dtype=np.int32)
+    col = np.zeros(max(tot, 1), dtype=np.int32)
+    val = np.zeros(max(tot, 1), dtype=np.float64)
+    _check(None, lib.tnqe_mpo_host(_ptr(h1), _ptr(eri), N, _ptr(dims), _ptr(nnz), _ptr(rowptr), _ptr(col),
+                                   _ptr(val), tot))
+    sites, ro, eo = [], 0, 0
+    for t in range(N):
+        n_r = 4 * int(dims[t + 1]) + 1
+        k = int(nnz[t])
+        sites.append((rowptr[ro:ro + n_r].copy(), col[eo:eo + k].copy(), val[eo:eo + k].copy()))
+        ro += n_r
+        eo += k
+    return dims.astype(int).tolist(), sites
 
 
 def tnqe_create(h1, eri, N: int, n_alpha: int, n_beta: int, options: Optional[tnqe_options] = None):
