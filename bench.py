@@ -277,8 +277,8 @@ def run_native(args):
     # captured case to this launch by the units it processes; None where no capture of the
     # current kernel exists for this workload.
     n_rot = sum(1 for i, j in pairs if i != j)
-    # rotate_pairs_kernel: 10.41 MB read + 0.54 MB written by a launch of 2 rotated pairs
-    traffic_table = {("n14_chi128", "rotate_pairs_kernel"): 10.95e6 / 2 * n_rot}
+    # rotate_pairs_kernel: 10.63 MB read + 0.76 MB written by a launch of 2 rotated pairs
+    traffic_table = {("n14_chi128", "rotate_pairs_kernel"): 11.39e6 / 2 * n_rot}
     traffic = traffic_table.get((w.name, top))
     t_ms, work, bound, peak, unit = kern[top]
     achieved = (work / (t_ms / 1e3)) / (1e12 if unit == "TFLOP/s" else 1e9) if t_ms > 0 else 0.0
