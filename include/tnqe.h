@@ -155,7 +155,11 @@ tnqe_status tnqe_get_rotated(tnqe_ctx* ctx, int* bond_dims, double* tensors, lon
  * resetting states, changing options, or any workspace reallocation drops the
  * graphs.  If the workspace of all pairs does not fit in 60% of free device
  * memory the pairs run in waves, synchronised between waves, and are not
- * captured. */
+ * captured.  In the BF16X* precisions the pairs (i, i), which need no
+ * rotation, are contracted on a second stream owned by the context (lowest
+ * priority) while the rotation kernel runs on the context's stream; that
+ * stream forks from and joins back into the context's stream within the call,
+ * so work the caller orders after the call on its stream sees every result. */
 tnqe_status tnqe_matrix_elements(tnqe_ctx* ctx, const int* pairs, int npairs,
                                  double* H_out, double* S_out);
 
