@@ -61,16 +61,23 @@ __device__ __forceinline__ void cp_async_zfill(void* dst, const void* src, int c
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src), "r"(src_bytes) : "memory");
 }
 
+// x 2^k: one multiplication by the exact power of two where 2^k is a normal
+// float (the product is then correctly rounded, as the scaling is), ldexpf beyond
+__device__ __forceinline__ float scale2(float x, int k) {
+  return (k >= -126 && k <= 127) ? __fmul_rn(x, __int_as_float((127 + k) << 23)) : ldexpf(x, k);
+}
 // Slices of one double-float value x = hi + lo (|x| 2^-e < 1/2): out[i] = S_i 2^-(8(i+1)).
 __device__ __forceinline__ void slice_df(float hi, float lo, int e, int ns, __nv_bfloat16* out, long long stride) {
-  float th = ldexpf(hi, 8 - e), tl = ldexpf(lo, 8 - e);
+  float th = scale2(hi, 8 - e), tl = scale2(lo, 8 - e);
+  float unit = 1.f / 256.f;                      // 2^-8(i+1), exact
   for (int i = 0; i < ns; ++i) {
     const float S = rintf(th);
     float sh, sl;
     two_sum_rn(__fsub_rn(th, S), tl, sh, sl);
-    out[i * stride] = __float2bfloat16_rn(ldexpf(S, -8 * (i + 1)));
+    out[i * stride] = __float2bfloat16_rn(__fmul_rn(S, unit));
     th = __fmul_rn(sh, 256.f);
     tl = __fmul_rn(sl, 256.f);
+    unit = __fmul_rn(unit, 1.f / 256.f);
   }
 }
 // slice_df of four consecutive values, each slice stored as one 8-byte word (out 8-byte aligned)
@@ -78,9 +85,10 @@ __device__ __forceinline__ void slice_df4(const float2* x, int e, int ns, __nv_b
   float th[4], tl[4];
 #pragma unroll
   for (int u = 0; u < 4; ++u) {
-    th[u] = ldexpf(x[u].x, 8 - e);
-    tl[u] = ldexpf(x[u].y, 8 - e);
+    th[u] = scale2(x[u].x, 8 - e);
+    tl[u] = scale2(x[u].y, 8 - e);
   }
+  float unit = 1.f / 256.f;                      // 2^-8(i+1), exact
   for (int i = 0; i < ns; ++i) {
     unsigned short o[4];
 #pragma unroll
@@ -88,10 +96,11 @@ __device__ __forceinline__ void slice_df4(const float2* x, int e, int ns, __nv_b
       const float S = rintf(th[u]);
       float sh, sl;
       two_sum_rn(__fsub_rn(th[u], S), tl[u], sh, sl);
-      o[u] = __bfloat16_as_ushort(__float2bfloat16_rn(ldexpf(S, -8 * (i + 1))));
+      o[u] = __bfloat16_as_ushort(__float2bfloat16_rn(__fmul_rn(S, unit)));
       th[u] = __fmul_rn(sh, 256.f);
       tl[u] = __fmul_rn(sl, 256.f);
     }
+    unit = __fmul_rn(unit, 1.f / 256.f);
     uint2 w;
     w.x = (unsigned)o[0] | ((unsigned)o[1] << 16);
     w.y = (unsigned)o[2] | ((unsigned)o[3] << 16);
