@@ -379,29 +379,14 @@ struct TermSink {
     }
     return gid;
   }
-  // site t's blocks of another sink, in its order (the sums of completing blocks add up)
-  void merge_site(const TermSink& o, const std::vector<int>& gid, int t) {
-    for (const auto& bl : o.blocks[t]) {
-      const int iin = gid[bl.first >> 32], iout = gid[bl.first & 0xffffffffu];
-      const uint64_t pk = ((uint64_t)iin << 32) | (uint64_t)iout;
-      int* it = site_blocks[t].find(pk);
-      if (!it) {
-        site_blocks[t].insert(pk, (int)blocks[t].size());
-        blocks[t].push_back({pk, bl.second});
-      } else {
-        const uint64_t kin = keys[iin], kout = keys[iout];
-        const bool trans = (key_type(kin) == 0 || key_type(kin) == 2) && (key_type(kout) == 1 || key_type(kout) == 3);
-        if (trans) {
-          Mat4& S = blocks[t][*it].second;
-          for (int q = 0; q < 16; ++q) S.m[q] += bl.second.m[q];
-        }
-      }
-    }
-  }
 };
 
 // Fixed number of term shares: the MPO comes out the same on every machine.
 constexpr int MPO_THREADS = 8;
+
+// partition of a block key among the merge tasks of one site
+constexpr int MERGE_PARTS = 8;
+inline int part_of(uint64_t pk) { return (int)(((pk * 0x9e3779b97f4a7c15ull) >> 40) % MERGE_PARTS); }
 
 // f(i) for i in [0, n) on MPO_THREADS threads (strided); the first exception is rethrown
 template <class F>
@@ -483,15 +468,42 @@ Mpo build_mpo(const double* h1, const double* eri, int N) {
   });
   TermSink& G = sinks[0];
   std::vector<std::vector<int>> gids(nsh);
+  gids[0].resize(G.keys.size());
+  for (size_t id = 0; id < G.keys.size(); ++id) gids[0][id] = (int)id;
   for (int w = 1; w < nsh; ++w) gids[w] = G.merge_keys(sinks[w]);
-  parallel_for(N, [&](int t) {
-    for (int w = 1; w < nsh; ++w) G.merge_site(sinks[w], gids[w], t);
+  // blocks of all shares, one task per (site, key partition): every task scans
+  // the site's blocks share by share and keeps its partition, so the sums of
+  // completing blocks run in share order whatever the thread timing
+  std::vector<std::vector<std::pair<uint64_t, Mat4>>> pblocks((size_t)N * MERGE_PARTS);
+  std::vector<FlatMap> pmap((size_t)N * MERGE_PARTS, FlatMap(256));
+  parallel_for(N * MERGE_PARTS, [&](int task) {
+    const int t = task / MERGE_PARTS, q = task % MERGE_PARTS;
+    std::vector<std::pair<uint64_t, Mat4>>& out = pblocks[task];
+    FlatMap& m = pmap[task];
+    for (int w = 0; w < nsh; ++w) {
+      const std::vector<int>& gid = gids[w];
+      for (const auto& bl : sinks[w].blocks[t]) {
+        const int iin = gid[bl.first >> 32], iout = gid[bl.first & 0xffffffffu];
+        const uint64_t pk = ((uint64_t)iin << 32) | (uint64_t)iout;
+        if (part_of(pk) != q) continue;
+        int* it = m.find(pk);
+        if (!it) {
+          m.insert(pk, (int)out.size());
+          out.push_back({pk, bl.second});
+        } else {
+          const uint64_t kin = G.keys[iin], kout = G.keys[iout];
+          const bool trans = (key_type(kin) == 0 || key_type(kin) == 2) && (key_type(kout) == 1 || key_type(kout) == 3);
+          if (trans) {
+            Mat4& S = out[*it].second;
+            for (int z = 0; z < 16; ++z) S.m[z] += bl.second.m[z];
+          }
+        }
+      }
+    }
   });
   std::vector<uint64_t>& keys = G.keys;
   std::vector<int>& kstart = G.kstart;
   std::vector<int>& kend = G.kend;
-  std::vector<FlatMap>& site_blocks = G.site_blocks;
-  std::vector<std::vector<std::pair<uint64_t, Mat4>>>& blocks = G.blocks;
   // identity string everywhere (gives the overlap), completed H to the end
   kstart[0] = 0;
   kend[0] = N;
@@ -513,41 +525,50 @@ Mpo build_mpo(const double* h1, const double* eri, int N) {
     mpo.dims[b] = c;
   }
   // per site (independent, in parallel): pass-through of every channel alive on
-  // both sides of the site, then the CSR rows
+  // both sides of the site, then the CSR rows (counted, filled, each row sorted)
   mpo.sites.resize(N);
   parallel_for(N, [&](int t) {
+    std::vector<std::pair<uint64_t, Mat4>> extra;
     for (size_t id = 0; id < keys.size(); ++id) {
       if (chan_of[t][id] < 0 || chan_of[t + 1][id] < 0) continue;
       const uint64_t pk = ((uint64_t)id << 32) | (uint64_t)id;
-      if (site_blocks[t].contains(pk)) continue;
+      if (pmap[(size_t)t * MERGE_PARTS + part_of(pk)].contains(pk)) continue;
       const int tp = key_type(keys[id]);
       const bool odd = (tp >= 2) && (key_nops(keys[id]) & 1);
-      site_blocks[t].insert(pk, (int)blocks[t].size());
-      blocks[t].push_back({pk, odd ? P4 : I4});
+      extra.push_back({pk, odd ? P4 : I4});
     }
     MpoSite& S = mpo.sites[t];
     S.Din = mpo.dims[t];
     S.Dout = mpo.dims[t + 1];
     const int nrow = 4 * S.Dout;
-    std::vector<std::vector<std::pair<int, double>>> rows(nrow);
-    for (auto& bl : blocks[t]) {
-      int iin = (int)(bl.first >> 32), iout = (int)(bl.first & 0xffffffffu);
-      int w = chan_of[t][iin], wo = chan_of[t + 1][iout];
-      if (w < 0 || wo < 0) throw std::runtime_error("MPO channel bookkeeping failed");
-      for (int k = 0; k < 4; ++k)
-        for (int kp = 0; kp < 4; ++kp) {
-          double v = bl.second.m[k * 4 + kp];
-          if (v != 0.0) rows[(size_t)k * S.Dout + wo].push_back({w * 4 + kp, v});
-        }
-    }
     S.rowptr.assign(nrow + 1, 0);
-    for (int r = 0; r < nrow; ++r) {
-      std::sort(rows[r].begin(), rows[r].end());
-      S.rowptr[r + 1] = S.rowptr[r] + (int)rows[r].size();
-      for (auto& e : rows[r]) {
-        S.col.push_back(e.first);
-        S.val.push_back(e.second);
-      }
+    auto each_entry = [&](auto&& f) {
+      auto visit = [&](const std::pair<uint64_t, Mat4>& bl) {
+        const int iin = (int)(bl.first >> 32), iout = (int)(bl.first & 0xffffffffu);
+        const int w = chan_of[t][iin], wo = chan_of[t + 1][iout];
+        if (w < 0 || wo < 0) throw std::runtime_error("MPO channel bookkeeping failed");
+        for (int k = 0; k < 4; ++k)
+          for (int kp = 0; kp < 4; ++kp) {
+            const double v = bl.second.m[k * 4 + kp];
+            if (v != 0.0) f(k * S.Dout + wo, w * 4 + kp, v);
+          }
+      };
+      for (int q = 0; q < MERGE_PARTS; ++q)
+        for (const auto& bl : pblocks[(size_t)t * MERGE_PARTS + q]) visit(bl);
+      for (const auto& bl : extra) visit(bl);
+    };
+    each_entry([&](int r, int, double) { ++S.rowptr[r + 1]; });
+    for (int r = 0; r < nrow; ++r) S.rowptr[r + 1] += S.rowptr[r];
+    const int nz = S.rowptr[nrow];
+    std::vector<std::pair<int, double>> ent(nz);
+    std::vector<int> cur(S.rowptr.begin(), S.rowptr.end() - 1);
+    each_entry([&](int r, int c, double v) { ent[cur[r]++] = {c, v}; });
+    for (int r = 0; r < nrow; ++r) std::sort(ent.begin() + S.rowptr[r], ent.begin() + S.rowptr[r + 1]);
+    S.col.resize(nz);
+    S.val.resize(nz);
+    for (int e = 0; e < nz; ++e) {
+      S.col[e] = ent[e].first;
+      S.val[e] = ent[e].second;
     }
   });
   return mpo;
