@@ -69,6 +69,18 @@ struct DBuf {
   template <class T> T* as() const { return reinterpret_cast<T*>(p); }
 };
 
+// Arrays packed back to back at 256-byte aligned offsets, for one upload.
+struct HostPack {
+  std::vector<unsigned char> h;
+  template <class T> size_t add(const std::vector<T>& v) {
+    const size_t o = (h.size() + 255) & ~(size_t)255;
+    const size_t n = v.size() * sizeof(T);
+    h.resize(o + std::max<size_t>(n, 16), 0);
+    if (n) std::memcpy(h.data() + o, v.data(), n);
+    return o;
+  }
+};
+
 template <class T> T* dalloc_copy(const std::vector<T>& v, std::vector<void*>& owned) {
   void* p = nullptr;
   CK(cudaMalloc(&p, std::max<size_t>(v.size() * sizeof(T), 16)));
@@ -1506,39 +1518,58 @@ void prepare_mps(tnqe_ctx* c, const double* const* tensors, const int* bond_dims
   rotate_integrals(c->h1.data(), c->eri.data(), U, N, hU, gU);
   m.mpo = build_mpo(hU.data(), gU.data(), N);
   if (m.mpo.dims[N] != 2) throw Error(TNQE_ERR_STATE, "MPO construction failed");
-  // upload
-  m.d_t = dalloc_copy(host, m.owned);
-  m.d_off = dalloc_copy(m.off, m.owned);
-  m.d_dims = dalloc_copy(m.dims, m.owned);
-  m.d_sec = dalloc_copy(m.sec, m.owned);
+  // upload: every array of the state packed into one host buffer (256-byte
+  // aligned offsets), then one allocation and one copy
+  HostPack pk;
+  const size_t o_t = pk.add(host), o_off = pk.add(m.off), o_dims = pk.add(m.dims), o_sec = pk.add(m.sec);
+  std::vector<size_t> o_rowptr(N), o_col(N), o_val(N), o_perm(N), o_v32(N), o_vdf(N), o_ent(N);
   for (int t = 0; t < N; ++t) {
-    m.d_rowptr.push_back(dalloc_copy(m.mpo.sites[t].rowptr, m.owned));
-    m.d_col.push_back(dalloc_copy(m.mpo.sites[t].col, m.owned));
-    m.d_val.push_back(dalloc_copy(m.mpo.sites[t].val, m.owned));
+    const MpoSite& S = m.mpo.sites[t];
+    o_rowptr[t] = pk.add(S.rowptr);
+    o_col[t] = pk.add(S.col);
+    o_val[t] = pk.add(S.val);
     {
-      const std::vector<int>& rp = m.mpo.sites[t].rowptr;
+      const std::vector<int>& rp = S.rowptr;
       std::vector<int> perm(rp.size() - 1);
       for (size_t r = 0; r < perm.size(); ++r) perm[r] = (int)r;
       std::stable_sort(perm.begin(), perm.end(), [&](int x, int y) { return rp[x + 1] - rp[x] > rp[y + 1] - rp[y]; });
-      m.d_rowperm.push_back(dalloc_copy(perm, m.owned));
+      o_perm[t] = pk.add(perm);
     }
-    std::vector<float> v32(m.mpo.sites[t].val.begin(), m.mpo.sites[t].val.end());
-    m.d_val32.push_back(dalloc_copy(v32, m.owned));
+    std::vector<float> v32(S.val.begin(), S.val.end());
+    o_v32[t] = pk.add(v32);
     std::vector<float2> vdf(v32.size());
     for (size_t e = 0; e < v32.size(); ++e) {
-      const double v = m.mpo.sites[t].val[e];
+      const double v = S.val[e];
       vdf[e].x = (float)v;
       vdf[e].y = (float)(v - (double)vdf[e].x);
     }
-    m.d_valdf.push_back(dalloc_copy(vdf, m.owned));
+    o_vdf[t] = pk.add(vdf);
     std::vector<float4> ent(vdf.size());
     for (size_t e = 0; e < vdf.size(); ++e) {
-      int col = m.mpo.sites[t].col[e];
+      int col = S.col[e];
       float cf;
       std::memcpy(&cf, &col, sizeof(cf));
       ent[e] = make_float4(vdf[e].x, vdf[e].y, cf, 0.f);
     }
-    m.d_ent.push_back(dalloc_copy(ent, m.owned));
+    o_ent[t] = pk.add(ent);
+  }
+  void* dev = nullptr;
+  CK(cudaMalloc(&dev, pk.h.size()));
+  m.owned.push_back(dev);
+  CK(cudaMemcpy(dev, pk.h.data(), pk.h.size(), cudaMemcpyHostToDevice));
+  unsigned char* base = static_cast<unsigned char*>(dev);
+  m.d_t = reinterpret_cast<double*>(base + o_t);
+  m.d_off = reinterpret_cast<long long*>(base + o_off);
+  m.d_dims = reinterpret_cast<int*>(base + o_dims);
+  m.d_sec = reinterpret_cast<SectorTable*>(base + o_sec);
+  for (int t = 0; t < N; ++t) {
+    m.d_rowptr.push_back(reinterpret_cast<int*>(base + o_rowptr[t]));
+    m.d_col.push_back(reinterpret_cast<int*>(base + o_col[t]));
+    m.d_val.push_back(reinterpret_cast<double*>(base + o_val[t]));
+    m.d_rowperm.push_back(reinterpret_cast<int*>(base + o_perm[t]));
+    m.d_val32.push_back(reinterpret_cast<float*>(base + o_v32[t]));
+    m.d_valdf.push_back(reinterpret_cast<float2*>(base + o_vdf[t]));
+    m.d_ent.push_back(reinterpret_cast<float4*>(base + o_ent[t]));
   }
 }
 
