@@ -1440,36 +1440,48 @@ void prepare_mps(tnqe_ctx* c, const double* const* tensors, const int* bond_dims
     double amax = 0.0;
     for (long long x = 0; x < (long long)cl * 4 * cr; ++x) amax = std::max(amax, std::fabs(A[x]));
     const double tol = 1e-12 * amax;
+    // the charge of right index r is that of the first row (l, k) with weight in
+    // column r; every other weighted entry of the column must carry the same.
+    // Rows are walked in order (contiguous memory), columns tracked in parallel.
     q[s + 1].assign(cr, -1);
-    for (int r = 0; r < cr; ++r) {
-      for (int l = 0; l < cl && q[s + 1][r] < 0; ++l)
-        for (int k = 0; k < 4; ++k)
-          if (std::fabs(A[((size_t)l * 4 + k) * cr + r]) > tol) {
-            const int qa = q[s][l] / QSTRIDE + (k & 1), qb = q[s][l] % QSTRIDE + (k >> 1);
-            q[s + 1][r] = qa * QSTRIDE + qb;
-            break;
-          }
-      if (q[s + 1][r] < 0) throw Error(TNQE_ERR_ARG, "site " + std::to_string(s) + ": bond index with no weight");
-      for (int l = 0; l < cl; ++l)
-        for (int k = 0; k < 4; ++k) {
-          const double v = A[((size_t)l * 4 + k) * cr + r];
-          const int qa = q[s][l] / QSTRIDE + (k & 1), qb = q[s][l] % QSTRIDE + (k >> 1);
-          if (std::fabs(v) > tol && qa * QSTRIDE + qb != q[s + 1][r])
+    for (int l = 0; l < cl; ++l)
+      for (int k = 0; k < 4; ++k) {
+        const int qlk = (q[s][l] / QSTRIDE + (k & 1)) * QSTRIDE + q[s][l] % QSTRIDE + (k >> 1);
+        const double* row = A + ((size_t)l * 4 + k) * cr;
+        for (int r = 0; r < cr; ++r) {
+          if (!(std::fabs(row[r]) > tol)) continue;
+          if (q[s + 1][r] < 0) q[s + 1][r] = qlk;
+          else if (q[s + 1][r] != qlk)
             throw Error(TNQE_ERR_ARG, "site " + std::to_string(s) + ": entry breaks the particle-number block structure");
         }
-    }
+      }
+    for (int r = 0; r < cr; ++r)
+      if (q[s + 1][r] < 0) throw Error(TNQE_ERR_ARG, "site " + std::to_string(s) + ": bond index with no weight");
   }
   if (q[N][0] != c->na * QSTRIDE + c->nb) throw Error(TNQE_ERR_ARG, "state is not in the (n_alpha, n_beta) sector");
   // left-orthonormal sites 0..N-2 (columns of different charge have disjoint support)
+  // (the Gram matrix of the columns accumulated row by row, contiguous in memory)
   for (int s = 0; s + 1 < N; ++s) {
     const int cl = bond_dims[s], cr = bond_dims[s + 1];
     const double* A = tensors[s];
+    std::vector<double> gram((size_t)cr * cr, 0.0);
+    std::vector<std::vector<int>> same(cr);        // columns of r's charge at or after r
+    for (int r1 = 0; r1 < cr; ++r1)
+      for (int r2 = r1; r2 < cr; ++r2)
+        if (q[s + 1][r1] == q[s + 1][r2]) same[r1].push_back(r2);
+    for (int lk = 0; lk < cl * 4; ++lk) {
+      const double* row = A + (size_t)lk * cr;
+      for (int r1 = 0; r1 < cr; ++r1) {
+        const double a1 = row[r1];
+        if (a1 == 0.0) continue;
+        double* g = gram.data() + (size_t)r1 * cr;
+        for (int r2 : same[r1]) g[r2] += a1 * row[r2];
+      }
+    }
     for (int r1 = 0; r1 < cr; ++r1)
       for (int r2 = r1; r2 < cr; ++r2) {
         if (q[s + 1][r1] != q[s + 1][r2]) continue;
-        double acc = 0.0;
-        for (int lk = 0; lk < cl * 4; ++lk) acc += A[(size_t)lk * cr + r1] * A[(size_t)lk * cr + r2];
-        if (std::fabs(acc - (r1 == r2 ? 1.0 : 0.0)) > 1e-10)
+        if (std::fabs(gram[(size_t)r1 * cr + r2] - (r1 == r2 ? 1.0 : 0.0)) > 1e-10)
           throw Error(TNQE_ERR_ARG, "site " + std::to_string(s) + " is not left-orthonormal");
       }
   }
@@ -1498,20 +1510,29 @@ void prepare_mps(tnqe_ctx* c, const double* const* tensors, const int* bond_dims
   }
   std::vector<double> host;
   m.off.assign(N, 0);
+  {
+    size_t total = 0;
+    for (int s = 0; s < N; ++s) total += (size_t)bond_dims[s] * 4 * bond_dims[s + 1];
+    host.resize(total);                          // every entry is written below
+  }
+  size_t hoff = 0;
   for (int s = 0; s < N; ++s) {
     const int cl = bond_dims[s], cr = bond_dims[s + 1];
-    m.off[s] = (long long)host.size();
+    m.off[s] = (long long)hoff;
     const double* A = tensors[s];
-    const size_t base = host.size();
-    host.resize(base + (size_t)cl * 4 * cr);
-    for (int l = 0; l < cl; ++l)
-      for (int k = 0; k < 4; ++k)
-        for (int r = 0; r < cr; ++r) {
-          double v = A[((size_t)perm[s][l] * 4 + k) * cr + perm[s + 1][r]];
-          const int qa = q[s][perm[s][l]] / QSTRIDE + (k & 1), qb = q[s][perm[s][l]] % QSTRIDE + (k >> 1);
-          if (qa * QSTRIDE + qb != q[s + 1][perm[s + 1][r]]) v = 0.0;   // below-tolerance noise outside the blocks
-          host[base + ((size_t)l * 4 + k) * cr + r] = v;
-        }
+    std::vector<int> qr(cr);
+    for (int r = 0; r < cr; ++r) qr[r] = q[s + 1][perm[s + 1][r]];
+    const int* pr = perm[s + 1].data();
+    for (int l = 0; l < cl; ++l) {
+      const int ql = q[s][perm[s][l]];
+      for (int k = 0; k < 4; ++k) {
+        const int qlk = (ql / QSTRIDE + (k & 1)) * QSTRIDE + ql % QSTRIDE + (k >> 1);
+        const double* src = A + ((size_t)perm[s][l] * 4 + k) * cr;
+        double* dst = host.data() + hoff + ((size_t)l * 4 + k) * cr;
+        for (int r = 0; r < cr; ++r) dst[r] = (qlk == qr[r]) ? src[pr[r]] : 0.0;   // below-tolerance noise outside the blocks
+      }
+    }
+    hoff += (size_t)cl * 4 * cr;
   }
   // Hamiltonian in basis U and its MPO
   std::vector<double> hU, gU;
