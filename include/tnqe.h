@@ -86,6 +86,17 @@ typedef struct {
  * graphs on. */
 void tnqe_default_options(tnqe_options* opt);
 
+/* The checks tnqe_add_mps makes on a state, on the host, no GPU needed:
+ * tensors / bond_dims / U as for tnqe_add_mps, for N orbitals and
+ * (n_alpha, n_beta) electrons.  Returns TNQE_OK, or TNQE_ERR_ARG with the
+ * reason in msg (msg_len bytes including the terminating zero; msg may be
+ * NULL): U not orthogonal to 1e-12, bond dimensions outside [1, 256] or not
+ * 1 at the ends, a bond index with no weight, an entry that breaks the
+ * particle-number block structure, a state outside the (n_alpha, n_beta)
+ * sector, or a site 0..N-2 that is not left-orthonormal to 1e-10. */
+tnqe_status tnqe_check_mps(int N, int n_alpha, int n_beta, const double* const* tensors, const int* bond_dims,
+                           const double* U, char* msg, int msg_len);
+
 /* The Hamiltonian MPO the library builds for integrals (h1, eri) (Eq. 1 in
  * second quantisation, Sec. II A; one per state basis inside tnqe_add_mps),
  * computed on the host, no GPU needed.  h1: N*N row-major; eri: N^4

@@ -1416,8 +1416,12 @@ void check_ctx(tnqe_ctx* c) {
 }
 
 // ----------------------------------------------------------------------------- add_mps validation
-void prepare_mps(tnqe_ctx* c, const double* const* tensors, const int* bond_dims, const double* U, DevMps& m) {
-  const int N = c->N;
+// Host part of adding a state: validate it (orthogonal U, bond dimensions,
+// particle-number block structure, (n_alpha, n_beta) sector, left-orthonormal
+// sites 0..N-2), sort every bond by charge and lay the tensors out in that
+// order (host, back to back; offsets in m.off).  Throws Error(TNQE_ERR_ARG).
+void order_mps_host(int N, int na, int nb, const double* const* tensors, const int* bond_dims, const double* U,
+                    DevMps& m, std::vector<double>& host) {
   if (!tensors || !bond_dims || !U) throw Error(TNQE_ERR_ARG, "null argument");
   if (bond_dims[0] != 1 || bond_dims[N] != 1) throw Error(TNQE_ERR_ARG, "bond_dims[0] and bond_dims[N] must be 1");
   for (int b = 0; b <= N; ++b)
@@ -1458,7 +1462,7 @@ void prepare_mps(tnqe_ctx* c, const double* const* tensors, const int* bond_dims
     for (int r = 0; r < cr; ++r)
       if (q[s + 1][r] < 0) throw Error(TNQE_ERR_ARG, "site " + std::to_string(s) + ": bond index with no weight");
   }
-  if (q[N][0] != c->na * QSTRIDE + c->nb) throw Error(TNQE_ERR_ARG, "state is not in the (n_alpha, n_beta) sector");
+  if (q[N][0] != na * QSTRIDE + nb) throw Error(TNQE_ERR_ARG, "state is not in the (n_alpha, n_beta) sector");
   // left-orthonormal sites 0..N-2 (columns of different charge have disjoint support)
   // (the Gram matrix of the columns accumulated row by row, contiguous in memory)
   for (int s = 0; s + 1 < N; ++s) {
@@ -1508,7 +1512,7 @@ void prepare_mps(tnqe_ctx* c, const double* const* tensors, const int* bond_dims
       ++T.dim[T.nsec - 1];
     }
   }
-  std::vector<double> host;
+  host.clear();
   m.off.assign(N, 0);
   {
     size_t total = 0;
@@ -1534,6 +1538,12 @@ void prepare_mps(tnqe_ctx* c, const double* const* tensors, const int* bond_dims
     }
     hoff += (size_t)cl * 4 * cr;
   }
+}
+
+void prepare_mps(tnqe_ctx* c, const double* const* tensors, const int* bond_dims, const double* U, DevMps& m) {
+  const int N = c->N;
+  std::vector<double> host;
+  order_mps_host(N, c->na, c->nb, tensors, bond_dims, U, m, host);
   // Hamiltonian in basis U and its MPO
   std::vector<double> hU, gU;
   rotate_integrals(c->h1.data(), c->eri.data(), U, N, hU, gU);
@@ -1611,6 +1621,34 @@ void tnqe_default_options(tnqe_options* o) {
   o->cuda_stream = nullptr;
   o->device = 0;
   o->use_graphs = 1;
+}
+
+tnqe_status tnqe_check_mps(int N, int n_alpha, int n_beta, const double* const* tensors, const int* bond_dims,
+                           const double* U, char* msg, int msg_len) {
+  auto put = [&](const std::string& t) {
+    if (msg && msg_len > 0) {
+      const size_t n = std::min(t.size(), (size_t)msg_len - 1);
+      std::memcpy(msg, t.data(), n);
+      msg[n] = 0;
+    }
+  };
+  try {
+    if (N < 1 || N > 32 || n_alpha < 0 || n_beta < 0 || n_alpha > N || n_beta > N) {
+      put("bad N or electron numbers");
+      return TNQE_ERR_ARG;
+    }
+    DevMps m;
+    std::vector<double> host;
+    order_mps_host(N, n_alpha, n_beta, tensors, bond_dims, U, m, host);
+    put("");
+    return TNQE_OK;
+  } catch (const Error& e) {
+    put(e.what());
+    return e.st;
+  } catch (const std::bad_alloc&) {
+    put("out of host memory");
+    return TNQE_ERR_NOMEM;
+  }
 }
 
 tnqe_status tnqe_mpo_host(const double* h1, const double* eri, int N, int* dims, long long* nnz, int* rowptr,

@@ -37,7 +37,7 @@ class tnqe_options(ctypes.Structure):
                 ("cuda_stream", ctypes.c_void_p), ("device", ctypes.c_int), ("use_graphs", ctypes.c_int)]
 
 
-EXPORTED = ["tnqe_default_options", "tnqe_mpo_host", "tnqe_create", "tnqe_add_mps", "tnqe_reset_mps", "tnqe_rotate",
+EXPORTED = ["tnqe_default_options", "tnqe_mpo_host", "tnqe_check_mps", "tnqe_create", "tnqe_add_mps", "tnqe_reset_mps", "tnqe_rotate",
             "tnqe_get_rotated", "tnqe_matrix_elements", "tnqe_solve", "tnqe_set_precision", "tnqe_last_timing", "tnqe_last_profile", "tnqe_apply_gate_noalloc",
             "tnqe_solve_ex", "tnqe_dependence", "tnqe_autotune", "tnqe_set_tuning", "tnqe_clear_graphs", "tnqe_graph_count", "tnqe_last_error",
             "tnqe_destroy"]
@@ -57,6 +57,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.tnqe_default_options.restype = None
     lib.tnqe_create.argtypes = [P, P, I, I, I, ctypes.POINTER(tnqe_options), ctypes.POINTER(P)]
     lib.tnqe_mpo_host.argtypes = [P, P, I, P, P, P, P, P, LL]
+    lib.tnqe_check_mps.argtypes = [I, I, I, P, P, P, ctypes.c_char_p, I]
     lib.tnqe_add_mps.argtypes = [P, P, P, P, ctypes.POINTER(I)]
     lib.tnqe_reset_mps.argtypes = [P]
     lib.tnqe_rotate.argtypes = [P, I, I, ctypes.POINTER(D)]
@@ -105,6 +106,19 @@ def tnqe_default_options() -> tnqe_options:
     o = tnqe_options()
     load().tnqe_default_options(ctypes.byref(o))
     return o
+
+
+def tnqe_check_mps(tensors, U, n_alpha: int, n_beta: int):
+    """Host-side checks of tnqe_add_mps on one state: (status, message); 0 = valid."""
+    lib = load()
+    ts = [_f64(t) for t in tensors]
+    N = len(ts)
+    dims = np.array([ts[0].shape[0]] + [t.shape[2] for t in ts], dtype=np.int32)
+    ptrs = (ctypes.c_void_p * N)(*[t.ctypes.data for t in ts])
+    U = _f64(U)
+    buf = ctypes.create_string_buffer(256)
+    st = lib.tnqe_check_mps(N, n_alpha, n_beta, ctypes.cast(ptrs, ctypes.c_void_p), _ptr(dims), _ptr(U), buf, 256)
+    return st, buf.value.decode()
 
 
 def tnqe_mpo_host(h1, eri, N: int):
