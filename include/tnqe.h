@@ -86,6 +86,23 @@ typedef struct {
  * graphs on. */
 void tnqe_default_options(tnqe_options* opt);
 
+/* The nearest-neighbour Givens plan of a relative rotation V = U_i^T U_j
+ * (Eq. 11, App. A3), as tnqe_matrix_elements applies it, computed on the
+ * host.  V: N*N row-major orthogonal.  Gate g acts on sites (site[g],
+ * site[g] + 1) as G(J^T), J = [[c, -s], [s, c]] at rows/columns (site,
+ * site + 1); side[g] = 0 puts the singular values into the left tensor, 1 into
+ * the right.  Gates come in application order, N(N-1)/2 of them; cap is the
+ * capacity of site, side, c, s (TNQE_ERR_ARG if smaller).  *neg_site is the
+ * orbital whose creators change sign (det V = -1), else -1.  No GPU needed. */
+tnqe_status tnqe_givens_host(const double* V, int N, int* site, int* side, double* c, double* s, int cap,
+                             int* ngates, int* neg_site);
+
+/* h' = U^T h U and (pq|rs)' = sum U_ap U_bq U_cr U_ds (ab|cd): the integrals in
+ * basis U (column p of U = orbital p), as tnqe_add_mps uses them for the MPO of
+ * a state.  h_out N*N, eri_out N^4 (row-major, caller's host memory). */
+tnqe_status tnqe_rotate_integrals_host(const double* h1, const double* eri, const double* U, int N, double* h_out,
+                                       double* eri_out);
+
 /* The checks tnqe_add_mps makes on a state, on the host, no GPU needed:
  * tensors / bond_dims / U as for tnqe_add_mps, for N orbitals and
  * (n_alpha, n_beta) electrons.  Returns TNQE_OK, or TNQE_ERR_ARG with the

@@ -1623,6 +1623,41 @@ void tnqe_default_options(tnqe_options* o) {
   o->use_graphs = 1;
 }
 
+tnqe_status tnqe_givens_host(const double* V, int N, int* site, int* side, double* c, double* s, int cap,
+                             int* ngates, int* neg_site) {
+  try {
+    if (!V || !ngates || !neg_site || N < 1 || N > 64) return TNQE_ERR_ARG;
+    const tnqe::GivensPlan P = tnqe::givens_plan(V, N);
+    *ngates = (int)P.gates.size();
+    *neg_site = P.neg_site;
+    if (!site || !side || !c || !s) return TNQE_OK;
+    if (cap < (int)P.gates.size()) return TNQE_ERR_ARG;
+    for (size_t g = 0; g < P.gates.size(); ++g) {
+      site[g] = P.gates[g].site;
+      side[g] = P.gates[g].side;
+      c[g] = P.gates[g].c;
+      s[g] = P.gates[g].s;
+    }
+    return TNQE_OK;
+  } catch (...) {
+    return TNQE_ERR_NOMEM;
+  }
+}
+
+tnqe_status tnqe_rotate_integrals_host(const double* h1, const double* eri, const double* U, int N, double* h_out,
+                                       double* eri_out) {
+  try {
+    if (!h1 || !eri || !U || !h_out || !eri_out || N < 1 || N > 64) return TNQE_ERR_ARG;
+    std::vector<double> h, g;
+    tnqe::rotate_integrals(h1, eri, U, N, h, g);
+    std::copy(h.begin(), h.end(), h_out);
+    std::copy(g.begin(), g.end(), eri_out);
+    return TNQE_OK;
+  } catch (...) {
+    return TNQE_ERR_NOMEM;
+  }
+}
+
 tnqe_status tnqe_check_mps(int N, int n_alpha, int n_beta, const double* const* tensors, const int* bond_dims,
                            const double* U, char* msg, int msg_len) {
   auto put = [&](const std::string& t) {

@@ -37,7 +37,8 @@ class tnqe_options(ctypes.Structure):
                 ("cuda_stream", ctypes.c_void_p), ("device", ctypes.c_int), ("use_graphs", ctypes.c_int)]
 
 
-EXPORTED = ["tnqe_default_options", "tnqe_mpo_host", "tnqe_check_mps", "tnqe_create", "tnqe_add_mps", "tnqe_reset_mps", "tnqe_rotate",
+EXPORTED = ["tnqe_default_options", "tnqe_mpo_host", "tnqe_check_mps", "tnqe_givens_host",
+            "tnqe_rotate_integrals_host", "tnqe_create", "tnqe_add_mps", "tnqe_reset_mps", "tnqe_rotate",
             "tnqe_get_rotated", "tnqe_matrix_elements", "tnqe_solve", "tnqe_set_precision", "tnqe_last_timing", "tnqe_last_profile", "tnqe_apply_gate_noalloc",
             "tnqe_solve_ex", "tnqe_dependence", "tnqe_autotune", "tnqe_set_tuning", "tnqe_clear_graphs", "tnqe_graph_count", "tnqe_last_error",
             "tnqe_destroy"]
@@ -58,6 +59,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.tnqe_create.argtypes = [P, P, I, I, I, ctypes.POINTER(tnqe_options), ctypes.POINTER(P)]
     lib.tnqe_mpo_host.argtypes = [P, P, I, P, P, P, P, P, LL]
     lib.tnqe_check_mps.argtypes = [I, I, I, P, P, P, ctypes.c_char_p, I]
+    lib.tnqe_givens_host.argtypes = [P, I, P, P, P, P, I, ctypes.POINTER(I), ctypes.POINTER(I)]
+    lib.tnqe_rotate_integrals_host.argtypes = [P, P, P, I, P, P]
     lib.tnqe_add_mps.argtypes = [P, P, P, P, ctypes.POINTER(I)]
     lib.tnqe_reset_mps.argtypes = [P]
     lib.tnqe_rotate.argtypes = [P, I, I, ctypes.POINTER(D)]
@@ -106,6 +109,33 @@ def tnqe_default_options() -> tnqe_options:
     o = tnqe_options()
     load().tnqe_default_options(ctypes.byref(o))
     return o
+
+
+def tnqe_givens_host(V):
+    """The library's Givens plan of V: ([(site, c, s, side)], neg_site); side 0 = left, 1 = right."""
+    lib = load()
+    V = _f64(V)
+    N = V.shape[0]
+    cap = max(1, N * (N - 1) // 2)
+    site = np.zeros(cap, dtype=np.int32)
+    side = np.zeros(cap, dtype=np.int32)
+    c = np.zeros(cap)
+    s = np.zeros(cap)
+    ng, neg = ctypes.c_int(0), ctypes.c_int(0)
+    _check(None, lib.tnqe_givens_host(_ptr(V), N, _ptr(site), _ptr(side), _ptr(c), _ptr(s), cap,
+                                      ctypes.byref(ng), ctypes.byref(neg)))
+    return [(int(site[g]), float(c[g]), float(s[g]), int(side[g])) for g in range(ng.value)], neg.value
+
+
+def tnqe_rotate_integrals_host(h1, eri, U):
+    """(h', eri') in basis U as the library computes them."""
+    lib = load()
+    h1, eri, U = _f64(h1), _f64(eri), _f64(U)
+    N = U.shape[0]
+    ho = np.zeros((N, N))
+    go = np.zeros((N, N, N, N))
+    _check(None, lib.tnqe_rotate_integrals_host(_ptr(h1), _ptr(eri), _ptr(U), N, _ptr(ho), _ptr(go)))
+    return ho, go
 
 
 def tnqe_check_mps(tensors, U, n_alpha: int, n_beta: int):
