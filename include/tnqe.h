@@ -97,6 +97,12 @@ void tnqe_default_options(tnqe_options* opt);
 tnqe_status tnqe_givens_host(const double* V, int N, int* site, int* side, double* c, double* s, int cap,
                              int* ngates, int* neg_site);
 
+/* The 16 x 16 two-site gate G(J^T) of one Givens rotation, J = [[c, -s], [s, c]]
+ * (c^2 + s^2 = 1), on the local states k = n_alpha + 2 n_beta of the two
+ * sites: G[(4 k1' + k2') * 16 + (4 k1 + k2)], the matrix the rotation kernel
+ * applies.  No GPU needed. */
+tnqe_status tnqe_gate_host(double c, double s, double* G);
+
 /* h' = U^T h U and (pq|rs)' = sum U_ap U_bq U_cr U_ds (ab|cd): the integrals in
  * basis U (column p of U = orbital p), as tnqe_add_mps uses them for the MPO of
  * a state.  h_out N*N, eri_out N^4 (row-major, caller's host memory). */

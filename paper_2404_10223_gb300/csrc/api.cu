@@ -1644,6 +1644,12 @@ tnqe_status tnqe_givens_host(const double* V, int N, int* site, int* side, doubl
   }
 }
 
+tnqe_status tnqe_gate_host(double c, double s, double* G) {
+  if (!G || !(std::fabs(c * c + s * s - 1.0) < 1e-12)) return TNQE_ERR_ARG;
+  tnqe::gate_matrix(c, s, G);
+  return TNQE_OK;
+}
+
 tnqe_status tnqe_rotate_integrals_host(const double* h1, const double* eri, const double* U, int N, double* h_out,
                                        double* eri_out) {
   try {

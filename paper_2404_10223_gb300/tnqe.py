@@ -38,7 +38,7 @@ class tnqe_options(ctypes.Structure):
 
 
 EXPORTED = ["tnqe_default_options", "tnqe_mpo_host", "tnqe_check_mps", "tnqe_givens_host",
-            "tnqe_rotate_integrals_host", "tnqe_create", "tnqe_add_mps", "tnqe_reset_mps", "tnqe_rotate",
+            "tnqe_rotate_integrals_host", "tnqe_gate_host", "tnqe_create", "tnqe_add_mps", "tnqe_reset_mps", "tnqe_rotate",
             "tnqe_get_rotated", "tnqe_matrix_elements", "tnqe_solve", "tnqe_set_precision", "tnqe_last_timing", "tnqe_last_profile", "tnqe_apply_gate_noalloc",
             "tnqe_solve_ex", "tnqe_dependence", "tnqe_autotune", "tnqe_set_tuning", "tnqe_clear_graphs", "tnqe_graph_count", "tnqe_last_error",
             "tnqe_destroy"]
@@ -61,6 +61,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.tnqe_check_mps.argtypes = [I, I, I, P, P, P, ctypes.c_char_p, I]
     lib.tnqe_givens_host.argtypes = [P, I, P, P, P, P, I, ctypes.POINTER(I), ctypes.POINTER(I)]
     lib.tnqe_rotate_integrals_host.argtypes = [P, P, P, I, P, P]
+    lib.tnqe_gate_host.argtypes = [D, D, P]
     lib.tnqe_add_mps.argtypes = [P, P, P, P, ctypes.POINTER(I)]
     lib.tnqe_reset_mps.argtypes = [P]
     lib.tnqe_rotate.argtypes = [P, I, I, ctypes.POINTER(D)]
@@ -125,6 +126,13 @@ def tnqe_givens_host(V):
     _check(None, lib.tnqe_givens_host(_ptr(V), N, _ptr(site), _ptr(side), _ptr(c), _ptr(s), cap,
                                       ctypes.byref(ng), ctypes.byref(neg)))
     return [(int(site[g]), float(c[g]), float(s[g]), int(side[g])) for g in range(ng.value)], neg.value
+
+
+def tnqe_gate_host(c: float, s: float):
+    """The library's 16 x 16 two-site gate, rows (k1', k2'), columns (k1, k2)."""
+    G = np.zeros((16, 16))
+    _check(None, load().tnqe_gate_host(float(c), float(s), _ptr(G)))
+    return G
 
 
 def tnqe_rotate_integrals_host(h1, eri, U):

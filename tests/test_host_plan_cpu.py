@@ -1,8 +1,9 @@
 """The library's host steps of the path on the CPU, against the oracle:
 a1, the nearest-neighbour Givens plan of a relative rotation V = U_i^T U_j
-(Eq. 11, App. A3; rebuilds V, signed permutations give angles 0 and pi/2),
-and a2, the integrals in a state's basis (h' = U^T h U and the four-index
-transform of (pq|rs))."""
+(Eq. 11, App. A3; rebuilds V, signed permutations give angles 0 and pi/2) and
+the 16 x 16 two-site gate of each rotation, and a2, the integrals in a state's
+basis (h' = U^T h U and the four-index transform of (pq|rs))."""
+import math
 import numpy as np
 import pytest
 import scipy.linalg
@@ -68,3 +69,16 @@ def test_integrals_in_a_basis_equal_the_oracle():
     hb, gb = tnqe.tnqe_rotate_integrals_host(hl, gl, U.T)        # and back
     assert np.abs(hb - h1).max() <= 1e-12 * np.abs(h1).max()
     assert np.abs(gb - eri).max() <= 1e-12 * np.abs(eri).max()
+
+
+@pytest.mark.parametrize("theta", [0.0, 0.37, -1.2, math.pi / 4, math.pi / 2, 2.9])
+def test_two_site_gate_equals_the_oracle_gate(theta):
+    """The oracle's gate is pinned to the paper's g_4 form (test_oracle_pins)."""
+    G = tnqe.tnqe_gate_host(math.cos(theta), math.sin(theta))
+    assert np.abs(G - om.gate16(math.cos(theta), math.sin(theta))).max() <= 1e-14
+    assert np.abs(G @ G.T - np.eye(16)).max() <= 1e-14
+
+
+def test_gate_rejects_non_rotation():
+    with pytest.raises(tnqe.TnqeError):
+        tnqe.tnqe_gate_host(1.0, 0.5)
