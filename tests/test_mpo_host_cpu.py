@@ -38,7 +38,7 @@ def interleave_perm(N):
     return P
 
 
-@pytest.mark.parametrize("N", [2, 3, 4])
+@pytest.mark.parametrize("N", [1, 2, 3, 4])
 def test_library_mpo_equals_jordan_wigner_hamiltonian(N):
     h1, eri = inputs.draw_integrals(np.random.default_rng(40 + N), N, 2 * N)
     m = lib_mpo(h1, eri, N)
