@@ -79,11 +79,24 @@ typedef struct {
   void* cuda_stream;        /* cudaStream_t to launch on; NULL = a stream owned by the context */
   int device;               /* CUDA device ordinal */
   int use_graphs;           /* 1: replay repeated tnqe_matrix_elements calls from a captured CUDA graph */
+  int contraction_form;     /* tnqe_form: FP64 contraction in charge blocks (default) or dense */
 } tnqe_options;
+
+/* Form of the FP64 contraction (TNQE_PREC_FP64; the split-precision modes are dense).
+ * BLOCKS: every bond index has a particle-number charge (n_alpha, n_beta) and every
+ *   MPO channel the charge change of its operator string (particle number and S_z
+ *   are conserved, Sec. II C / Sec. IV A), so an environment entry L[a][w][b] can
+ *   be nonzero only when q(a) = q(b) + d(w).  Only those blocks are computed.
+ * DENSE: the same contraction over the zero-padded dense tensors (the masked
+ *   zeros are multiplied); the plain reference form. */
+typedef enum {
+  TNQE_FORM_BLOCKS = 0,
+  TNQE_FORM_DENSE = 1
+} tnqe_form;
 
 /* Fill *opt with defaults: FP64, chi_rot 0, cutoff 1e-14, solve_eps 1e-10,
  * no renormalisation, 60 Jacobi sweeps, max_spin 1<<26, own stream, device 0,
- * graphs on. */
+ * graphs on, charge-block contraction. */
 void tnqe_default_options(tnqe_options* opt);
 
 /* The nearest-neighbour Givens plan of a relative rotation V = U_i^T U_j
@@ -189,8 +202,8 @@ tnqe_status tnqe_get_rotated(tnqe_ctx* ctx, int* bond_dims, double* tensors, lon
  * resetting states, changing options, or any workspace reallocation drops the
  * graphs.  If the workspace of all pairs does not fit in 60% of free device
  * memory the pairs run in waves, synchronised between waves, and are not
- * captured.  In the BF16X* precisions the pairs (i, i), which need no
- * rotation, are contracted on a second stream owned by the context (lowest
+ * captured.  In the BF16X* precisions and the charge-block FP64 form the pairs
+ * (i, i), which need no rotation, are contracted on a second stream owned by the context (lowest
  * priority) while the rotation kernel runs on the context's stream; that
  * stream forks from and joins back into the context's stream within the call,
  * so work the caller orders after the call on its stream sees every result. */
@@ -247,6 +260,9 @@ tnqe_status tnqe_dependence(tnqe_ctx* ctx, const double* S, int M, double eps, d
 /* Change the contraction precision (tnqe_precision) of later calls. */
 tnqe_status tnqe_set_precision(tnqe_ctx* ctx, int precision);
 
+/* Change the form of the FP64 contraction (tnqe_form) of later calls. */
+tnqe_status tnqe_set_form(tnqe_ctx* ctx, int form);
+
 /* Device time (ms) of the phases of the last tnqe_matrix_elements call,
  * measured with CUDA events on the context stream:
  * times[0] rotation, times[1] contraction, times[2] whole call.
@@ -258,8 +274,9 @@ tnqe_status tnqe_last_timing(const tnqe_ctx* ctx, double* times, int* launches);
  * [0] rotation kernel ms, [1] stage-1 GEMM ms (X = L B), [2] stage-2 MPO ms,
  * [3] stage-3 GEMM ms (L' = A^T Y), [4] rotation algorithmic FLOPs
  * (two-site contraction + gate + 4mn^2 + 8n^3 per SVD block), [5] stage-1 FLOPs,
- * [6] stage-2 algorithmic bytes (X read once, Y written once), [7] stage-3 FLOPs,
- * [8] stage-2 FLOPs, [9] kernels launched, [10] slicing kernels ms and
+ * [6] stage-2 algorithmic bytes (X read once, Y written once; dense forms),
+ * [7] stage-3 FLOPs, [8] stage-2 FLOPs (in the charge-block form the FLOPs of
+ * the blocks computed, counted on the device), [9] kernels launched, [10] slicing kernels ms and
  * [11] slicing algorithmic bytes (BF16X* modes: source read once, slices
  * written once).  Times come from CUDA events on the context stream around
  * each launch and are summed over sites. */
@@ -268,11 +285,12 @@ tnqe_status tnqe_last_profile(const tnqe_ctx* ctx, double* prof, int n);
 
 /* ---------------------------------------------------------------------------
  * One Givens gate without any allocation.  The paper has no counterpart: this
- * entry point exists for callers that cannot call cudaMalloc -- code issuing
- * work while a stream is captured into a CUDA graph (an allocation there ends
- * or invalidates the capture), programs whose device memory is handed out by
- * their own pre-reserved pool, and host loops that must not pay allocation
- * latency.  Everything else in this header allocates through the context.
+ * entry point exists for callers that cannot call cudaMalloc -- programs whose
+ * device memory is all handed out by their own pool reserved at start-up (a
+ * serving process that owns the GPU's memory, where a library allocation would
+ * fail or fragment that pool), and host loops that must not pay the latency
+ * and implicit device synchronisation of cudaMalloc / cudaFree.  Everything
+ * else in this header allocates through the context.
  *
  * Applies G(J^T), J = [[c, -s], [s, c]] on two neighbouring orbitals, to the
  * two-site tensor A . B and splits it again by a truncated SVD, exactly as one
@@ -289,13 +307,16 @@ tnqe_status tnqe_last_profile(const tnqe_ctx* ctx, double* prof, int n);
  *
  * Its working storage is one static device array of
  * TNQE_NOALLOC_SCRATCH_BYTES (about 6.3 MiB) that every GPU loading this
- * library keeps until the process exits.  The first call on a device resolves
- * that array's address (cudaGetSymbolAddress) for the current device, so make
- * that first call before any stream capture begins.  All calls share the one
- * array: calls that may overlap on the GPU (other streams, other host threads,
- * the same stream from several captures) race and must be serialised by the
- * caller.  The call synchronises `stream` (a cudaStream_t, NULL = legacy
- * default stream) before returning. */
+ * library keeps until the process exits.  The first call on a device (and
+ * the first after a device reset) looks up that array's address for the
+ * current device and context (cudaGetSymbolAddress); make that first call
+ * before any stream capture begins on the device.  All calls share the one
+ * array and each starts by overwriting its header: calls that may overlap on
+ * the GPU (other streams, other host threads) race and must be serialised by
+ * the caller.  The call copies its 16 KiB parameter block to the device,
+ * launches one kernel, copies the result header back into host memory and
+ * synchronises `stream` (a cudaStream_t, NULL = legacy default stream)
+ * before returning. */
 #define TNQE_NOALLOC_MAX_CHI 128
 #define TNQE_NOALLOC_SCRATCH_BYTES 6569984
 tnqe_status tnqe_apply_gate_noalloc(const double* A, const double* B, int chi_l, int chi_m, int chi_r,

@@ -163,10 +163,13 @@ def gate16(c: float, s: float) -> np.ndarray:
 
 # ----------------------------------------------------------------------------- gate application
 def apply_rotation(tensors: Sequence[np.ndarray], V: np.ndarray, chi_rot: int, cutoff: float,
-                   renormalize: bool = False):
+                   renormalize: bool = False, trace: Optional[list] = None):
     """Truncated G(V)|MPS> for a left-canonical MPS (centre on the last site).
 
-    Returns (new tensors, total discarded weight sum sigma^2).
+    Returns (new tensors, total discarded weight sum sigma^2).  If ``trace`` is
+    a list, each gate appends ``(k, sigma)``: the kept count and the full
+    singular-value list of its SVD (diagnostics only; the arithmetic is the
+    same either way).
     """
     ts = [np.array(t, dtype=float, copy=True) for t in tensors]
     N = len(ts)
@@ -191,6 +194,8 @@ def apply_rotation(tensors: Sequence[np.ndarray], V: np.ndarray, chi_rot: int, c
             k = int(min(chi_rot, np.count_nonzero(sig > cutoff * sig[0])))
             k = max(k, 1)
         discarded += float(np.sum(sig[k:] ** 2))
+        if trace is not None:
+            trace.append((k, sig.copy()))
         u, sk, vt = u[:, :k], sig[:k], vt[:k]
         if side == "L":
             ts[a] = (u * sk).reshape(chl, 4, k)
@@ -432,12 +437,12 @@ class Context:
     def chi_of(self, j: int) -> int:
         return max(t.shape[2] for t in self.states[j][:-1]) if self.N > 1 else 1
 
-    def rotate(self, i: int, j: int):
+    def rotate(self, i: int, j: int, trace: Optional[list] = None):
         if i == j:
             return self.states[j], 0.0
         V = self.Us[i].T @ self.Us[j]
         chi_rot = self.chi_rot if self.chi_rot > 0 else self.chi_of(j)
-        return apply_rotation(self.states[j], V, chi_rot, self.cutoff, self.renormalize)
+        return apply_rotation(self.states[j], V, chi_rot, self.cutoff, self.renormalize, trace)
 
     def pair(self, i: int, j: int):
         ket, disc = self.rotate(i, j)

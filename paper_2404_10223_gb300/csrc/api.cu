@@ -112,12 +112,112 @@ struct DevMps {
   std::vector<float*> d_val32;
   std::vector<float2*> d_valdf;          // (hi, lo) FP32 pairs of the MPO values
   std::vector<float4*> d_ent;            // (hi, lo, column bits, 0) per MPO nonzero
+  std::vector<BsChannels> bs_ch;         // N + 1: channel classes by charge change (device pointers)
+  std::vector<BsRows> bs_rows;           // N: MPO rows by charge class (device pointers)
   std::vector<void*> owned;
   void free_all() {
     for (void* p : owned) cudaFree(p);
     owned.clear();
   }
 };
+
+// Charge change d(w) = (d_alpha, d_beta) of every MPO channel: the charge that the
+// operator string of channel w adds to the left part of a state.  Propagated
+// from bond 0 (identity string, no change) through the nonzeros W[(k, w'), (w, k')],
+// which set d(w') = d(w) + q(k) - q(k'); channels the forward pass does not reach
+// take theirs from the right.  Every nonzero is then checked against the rule.
+struct BlockTables {
+  std::vector<std::vector<int>> ch_off, ch_d, ch_w;           // per bond
+  std::vector<std::vector<int>> rc_off, rc_d, rc_rows, rc_nnz; // per site
+};
+
+BlockTables block_tables(const Mpo& mpo, int N) {
+  const int UNSET = 1 << 20;
+  std::vector<std::vector<int>> da(N + 1), db(N + 1);
+  for (int b = 0; b <= N; ++b) {
+    da[b].assign(mpo.dims[b], UNSET);
+    db[b].assign(mpo.dims[b], UNSET);
+  }
+  da[0][0] = db[0][0] = 0;
+  auto qa = [](int k) { return k & 1; };
+  auto qb = [](int k) { return k >> 1; };
+  for (int t = 0; t < N; ++t) {
+    const MpoSite& S = mpo.sites[t];
+    for (int row = 0; row < 4 * S.Dout; ++row) {
+      const int k = row / S.Dout, wp = row % S.Dout;
+      for (int e = S.rowptr[row]; e < S.rowptr[row + 1]; ++e) {
+        const int w = S.col[e] / 4, kp = S.col[e] % 4;
+        if (da[t][w] == UNSET || da[t + 1][wp] != UNSET) continue;
+        da[t + 1][wp] = da[t][w] + qa(k) - qa(kp);
+        db[t + 1][wp] = db[t][w] + qb(k) - qb(kp);
+      }
+    }
+  }
+  for (int t = N - 1; t >= 0; --t) {
+    const MpoSite& S = mpo.sites[t];
+    for (int row = 0; row < 4 * S.Dout; ++row) {
+      const int k = row / S.Dout, wp = row % S.Dout;
+      for (int e = S.rowptr[row]; e < S.rowptr[row + 1]; ++e) {
+        const int w = S.col[e] / 4, kp = S.col[e] % 4;
+        if (da[t][w] != UNSET || da[t + 1][wp] == UNSET) continue;
+        da[t][w] = da[t + 1][wp] - qa(k) + qa(kp);
+        db[t][w] = db[t + 1][wp] - qb(k) + qb(kp);
+      }
+    }
+  }
+  for (int b = 0; b <= N; ++b)
+    for (int w = 0; w < mpo.dims[b]; ++w)
+      if (da[b][w] == UNSET) da[b][w] = db[b][w] = 0;         // a channel no nonzero touches
+  BlockTables T;
+  T.ch_off.resize(N + 1);
+  T.ch_d.resize(N + 1);
+  T.ch_w.resize(N + 1);
+  for (int b = 0; b <= N; ++b) {
+    std::map<std::pair<int, int>, std::vector<int>> cls;
+    for (int w = 0; w < mpo.dims[b]; ++w) cls[{da[b][w], db[b][w]}].push_back(w);
+    T.ch_off[b].push_back(0);
+    for (const auto& kv : cls) {
+      T.ch_d[b].push_back(kv.first.first);
+      T.ch_d[b].push_back(kv.first.second);
+      T.ch_w[b].insert(T.ch_w[b].end(), kv.second.begin(), kv.second.end());
+      T.ch_off[b].push_back((int)T.ch_w[b].size());
+    }
+  }
+  T.rc_off.resize(N);
+  T.rc_d.resize(N);
+  T.rc_rows.resize(N);
+  T.rc_nnz.resize(N);
+  for (int t = 0; t < N; ++t) {
+    const MpoSite& S = mpo.sites[t];
+    std::map<std::pair<int, int>, std::vector<int>> cls;
+    for (int row = 0; row < 4 * S.Dout; ++row) {
+      const int k = row / S.Dout, wp = row % S.Dout;
+      const int rda = da[t + 1][wp] - qa(k), rdb = db[t + 1][wp] - qb(k);
+      for (int e = S.rowptr[row]; e < S.rowptr[row + 1]; ++e) {
+        const int w = S.col[e] / 4, kp = S.col[e] % 4;
+        if (da[t][w] - qa(kp) != rda || db[t][w] - qb(kp) != rdb)
+          throw Error(TNQE_ERR_STATE, "MPO nonzero breaks particle-number conservation at site " + std::to_string(t));
+      }
+      cls[{rda, rdb}].push_back(row);
+    }
+    if ((int)cls.size() > BS_MAXRC) throw Error(TNQE_ERR_STATE, "too many MPO row charge classes");
+    T.rc_off[t].push_back(0);
+    for (auto& kv : cls) {
+      std::vector<int>& rows = kv.second;
+      std::stable_sort(rows.begin(), rows.end(), [&](int x, int y) {
+        return S.rowptr[x + 1] - S.rowptr[x] > S.rowptr[y + 1] - S.rowptr[y];
+      });
+      int nz = 0;
+      for (int r : rows) nz += S.rowptr[r + 1] - S.rowptr[r];
+      T.rc_d[t].push_back(kv.first.first);
+      T.rc_d[t].push_back(kv.first.second);
+      T.rc_rows[t].insert(T.rc_rows[t].end(), rows.begin(), rows.end());
+      T.rc_off[t].push_back((int)T.rc_rows[t].size());
+      T.rc_nnz[t].push_back(nz);
+    }
+  }
+  return T;
+}
 
 struct PairPlan {                        // cached per (i, j): Givens gates on the device
   int ngates = 0, neg_site = -1;
@@ -143,6 +243,7 @@ struct FinishInfo {
   int launches = 0;
   bool check_err = false;
   bool single_wave = true;
+  std::vector<const double*> bs_flops;        // device FLOP counters (stages 1, 2, 3) of the block-sparse form
 };
 
 struct GraphEntry {
@@ -178,6 +279,7 @@ struct tnqe_ctx {
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   DBuf oz_ws_side, oz_desc_side, split_out, split_idx;
+  DBuf con_ws_side, con_desc_side, bs_flops, bs_flops_side;   // block-sparse FP64 form
   bool no_events = false;                  // profiling events off (work on the side stream)
   bool err_preset = false;                 // the pipeline error word was cleared before the fork
   DBuf solve_buf;                          // tnqe_solve / tnqe_dependence, sized once for M = 32
@@ -455,6 +557,7 @@ struct KetView {
   const double* base;
   std::vector<long long> off;   // per site
   std::vector<int> dims;        // N + 1
+  const SectorTable* sec = nullptr;   // N + 1 device sector tables (the rotation's for a rotated ket)
 };
 
 // Per-site event pairs of the last wave go to the finish step; earlier waves
@@ -652,6 +755,160 @@ void run_contractions(tnqe_ctx* c, const std::vector<std::pair<int, int>>& pairs
       ip1 += n1 + 1;
       ip3 += n3 + 1;
       ips += ns + 1;
+    }
+    CKL(launch_extract(reinterpret_cast<const double* const*>(dd + of), nw, d_H + p0, d_S + p0, c->stream));
+    c->launches += 1;
+    std::vector<std::array<int, 3>> reads;
+    for (int t = 0; t < N; ++t) {
+      const int e = 2 + 6 * t;
+      reads.push_back({e, e + 1, 1});
+      reads.push_back({e + 1, e + 2, 2});
+      reads.push_back({e + 2, e + 3, 3});
+    }
+    site_events(c, fi, p1 == (size_t)np, reads);
+    p0 = p1;
+  }
+}
+
+// ----------------------------------------------------------------------------- block-sparse FP64 contraction
+// The dense form's workspace and layout, with only the charge-allowed blocks
+// computed (kernels_block.cu).  Work items per site: stage 1 and stage 3 one
+// CTA per (pair, bra sector, channel class), stage 2 one CTA per (pair, bra
+// index).  Algorithmic FLOPs are counted on the device (the ket's sector
+// dimensions are decided there) and read back when the call has finished.
+void run_contractions_bs(tnqe_ctx* c, const std::vector<std::pair<int, int>>& pairs, const std::vector<KetView>& kets,
+                         double* d_H, double* d_S, FinishInfo& fi) {
+  const int N = c->N;
+  const int np = (int)pairs.size();
+  std::vector<long long> envsz(np), xsz(np), ysz(np);
+  for (int p = 0; p < np; ++p) {
+    const DevMps& bi = *c->mps[pairs[p].first];
+    const KetView& kv = kets[p];
+    long long e = 1, x = 1, y = 1;
+    for (int t = 0; t <= N; ++t) e = std::max(e, (long long)bi.dims[t] * bi.mpo.dims[t] * kv.dims[t]);
+    for (int t = 0; t < N; ++t) {
+      x = std::max(x, (long long)bi.dims[t] * bi.mpo.dims[t] * 4 * kv.dims[t + 1]);
+      y = std::max(y, (long long)bi.dims[t] * 4 * bi.mpo.dims[t + 1] * kv.dims[t + 1]);
+    }
+    envsz[p] = e;
+    xsz[p] = x;
+    ysz[p] = y;
+  }
+  c->bs_flops.ensure(4 * sizeof(double));
+  CK(cudaMemsetAsync(c->bs_flops.p, 0, 4 * sizeof(double), c->stream));
+  double* dfl = c->bs_flops.as<double>();
+  fi.bs_flops.push_back(dfl);
+  size_t freeb = 0, totalb = 0;
+  CK(cudaMemGetInfo(&freeb, &totalb));
+  const double budget = 0.6 * (double)(freeb + c->con_ws.cap);
+  size_t p0 = 0;
+  while (p0 < (size_t)np) {
+    size_t p1 = p0;
+    double need = 0.0;
+    while (p1 < (size_t)np) {
+      const double add = 8.0 * (2.0 * envsz[p1] + xsz[p1] + ysz[p1]);
+      if (p1 > p0 && need + add > budget) break;
+      need += add;
+      ++p1;
+    }
+    const int nw = (int)(p1 - p0);
+    c->con_ws.ensure((size_t)need + 256);
+    std::vector<double*> env0(nw), env1(nw), X(nw), Y(nw);
+    {
+      double* base = c->con_ws.as<double>();
+      long long o = 0;
+      for (int w = 0; w < nw; ++w) {
+        const int p = (int)p0 + w;
+        env0[w] = base + o;
+        o += envsz[p];
+        env1[w] = base + o;
+        o += envsz[p];
+        X[w] = base + o;
+        o += xsz[p];
+        Y[w] = base + o;
+        o += ysz[p];
+      }
+    }
+    // descriptors: site-major, pairs inside; CTA prefixes per site and stage
+    std::vector<BsSiteDesc> ds((size_t)N * nw);
+    std::vector<long long> pre1, pre2, pre3;
+    std::vector<long long> tot1(N), tot2(N), tot3(N);
+    for (int t = 0; t < N; ++t) {
+      long long n1 = 0, n2 = 0, n3 = 0;
+      for (int w = 0; w < nw; ++w) {
+        const int p = (int)p0 + w;
+        const DevMps& bi = *c->mps[pairs[p].first];
+        const KetView& kv = kets[p];
+        BsSiteDesc& d = ds[(size_t)t * nw + w];
+        d.Din = bi.mpo.dims[t];
+        d.Dout = bi.mpo.dims[t + 1];
+        d.ca = bi.dims[t];
+        d.ca2 = bi.dims[t + 1];
+        d.capb = kv.dims[t];
+        d.capb2 = kv.dims[t + 1];
+        d.A = bi.d_t + bi.off[t];
+        d.B = kv.base + kv.off[t];
+        d.braL = bi.d_sec + t;
+        d.braR = bi.d_sec + t + 1;
+        d.ketL = kv.sec + t;
+        d.ketR = kv.sec + t + 1;
+        d.Lin = (t & 1) ? env1[w] : env0[w];
+        d.Lout = (t & 1) ? env0[w] : env1[w];
+        d.X = X[w];
+        d.Y = Y[w];
+        d.rowptr = bi.d_rowptr[t];
+        d.col = bi.d_col[t];
+        d.val = bi.d_val[t];
+        d.chL = bi.bs_ch[t];
+        d.chR = bi.bs_ch[t + 1];
+        d.rows = bi.bs_rows[t];
+        pre1.push_back(n1);
+        pre2.push_back(n2);
+        pre3.push_back(n3);
+        n1 += (long long)bi.sec[t].nsec * d.chL.ncls;
+        n2 += d.ca;
+        n3 += (long long)bi.sec[t + 1].nsec * d.chR.ncls;
+      }
+      pre1.push_back(n1);
+      pre2.push_back(n2);
+      pre3.push_back(n3);
+      tot1[t] = n1;
+      tot2[t] = n2;
+      tot3[t] = n3;
+    }
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    const size_t bd = ds.size() * sizeof(BsSiteDesc), bp = pre1.size() * 8, bf = (size_t)nw * sizeof(double*);
+    const size_t od = 0, op1 = al(bd), op2 = op1 + al(bp), op3 = op2 + al(bp), oe = op3 + al(bp), of = oe + al(bf);
+    const size_t total = of + al(bf);
+    std::vector<unsigned char> host(total, 0);
+    std::memcpy(host.data() + od, ds.data(), bd);
+    std::memcpy(host.data() + op1, pre1.data(), bp);
+    std::memcpy(host.data() + op2, pre2.data(), bp);
+    std::memcpy(host.data() + op3, pre3.data(), bp);
+    std::memcpy(host.data() + oe, env0.data(), bf);
+    std::vector<const double*> fin(nw);
+    for (int w = 0; w < nw; ++w) fin[w] = (N & 1) ? env1[w] : env0[w];
+    std::memcpy(host.data() + of, fin.data(), bf);
+    c->con_desc.ensure(total);
+    unsigned char* dd = c->con_desc.as<unsigned char>();
+    upload(c, dd, host.data(), total);
+    CKL(launch_unit_env_f64(reinterpret_cast<double* const*>(dd + oe), nw, c->stream));   // L_0 = 1
+    c->launches += 1;
+    const BsSiteDesc* dsd = reinterpret_cast<const BsSiteDesc*>(dd + od);
+    for (int t = 0; t < N; ++t) {
+      const size_t pofs = (size_t)t * (nw + 1);
+      cudaEvent_t* E = &c->pev[2 + 6 * t];
+      record_event(c, E[0]);
+      CKL(launch_bs_stage1(dsd + (size_t)t * nw, reinterpret_cast<const long long*>(dd + op1) + pofs, nw, tot1[t], dfl,
+                           c->stream));
+      record_event(c, E[1]);
+      CKL(launch_bs_stage2(dsd + (size_t)t * nw, reinterpret_cast<const long long*>(dd + op2) + pofs, nw, tot2[t], dfl,
+                           c->stream));
+      record_event(c, E[2]);
+      CKL(launch_bs_stage3(dsd + (size_t)t * nw, reinterpret_cast<const long long*>(dd + op3) + pofs, nw, tot3[t], dfl,
+                           c->stream));
+      record_event(c, E[3]);
+      c->launches += 3;
     }
     CKL(launch_extract(reinterpret_cast<const double* const*>(dd + of), nw, d_H + p0, d_S + p0, c->stream));
     c->launches += 1;
@@ -1218,6 +1475,9 @@ struct SideScope {
     std::swap(c->stream, c->side);
     std::swap(c->oz_ws, c->oz_ws_side);
     std::swap(c->oz_desc, c->oz_desc_side);
+    std::swap(c->con_ws, c->con_ws_side);
+    std::swap(c->con_desc, c->con_desc_side);
+    std::swap(c->bs_flops, c->bs_flops_side);
     c->no_events = !c->no_events;
   }
 };
@@ -1237,7 +1497,8 @@ void enqueue_matrix_elements(tnqe_ctx* c, const std::vector<std::pair<int, int>>
   // caller's order at the end.
   std::vector<int> di, ri;
   for (int p = 0; p < npairs; ++p) (pl[p].first == pl[p].second ? di : ri).push_back(p);
-  const bool split = c->opt.precision >= TNQE_PREC_BF16X3 && !di.empty() && !ri.empty();
+  const bool blocks = c->opt.precision == TNQE_PREC_FP64 && c->opt.contraction_form == TNQE_FORM_BLOCKS;
+  const bool split = (c->opt.precision >= TNQE_PREC_BF16X3 || blocks) && !di.empty() && !ri.empty();
   std::vector<std::pair<int, int>> pr;
   double *oH = dH, *oS = dS;
   if (split) {
@@ -1277,13 +1538,15 @@ void enqueue_matrix_elements(tnqe_ctx* c, const std::vector<std::pair<int, int>>
     for (int p : di) {
       pd.push_back(pl[p]);
       const DevMps& mi = *c->mps[pl[p].first];
-      kd.push_back(KetView{mi.d_t, mi.off, mi.dims});
+      kd.push_back(KetView{mi.d_t, mi.off, mi.dims, mi.d_sec});
     }
     {
       FinishInfo fs;
       SideScope scope(c);
-      run_contractions_oz(c, pd, kd, oH, oS, fs);
+      if (blocks) run_contractions_bs(c, pd, kd, oH, oS, fs);
+      else run_contractions_oz(c, pd, kd, oH, oS, fs);
       if (!fs.single_wave) fi.single_wave = false;
+      fi.bs_flops.insert(fi.bs_flops.end(), fs.bs_flops.begin(), fs.bs_flops.end());
     }
     CK(cudaEventRecord(c->ev_join, c->side));
   }
@@ -1293,15 +1556,18 @@ void enqueue_matrix_elements(tnqe_ctx* c, const std::vector<std::pair<int, int>>
     kets[p].base = mi.d_t;
     kets[p].off = mi.off;
     kets[p].dims = mi.dims;
+    kets[p].sec = mi.d_sec;
   }
   for (size_t k = 0; k < rb.pair_idx.size(); ++k) {
     KetView& kv = kets[rb.pair_idx[k]];
     kv.base = rb.work[k];
     kv.off = rb.woff[k];
     kv.dims = rb.cap[k];
+    kv.sec = rb.sec[k];
   }
   record_event(c, c->ev[2]);
-  if (c->opt.precision == TNQE_PREC_TF32X3) run_contractions_tc(c, pm, kets, mH, mS, fi);
+  if (blocks) run_contractions_bs(c, pm, kets, mH, mS, fi);
+  else if (c->opt.precision == TNQE_PREC_TF32X3) run_contractions_tc(c, pm, kets, mH, mS, fi);
   else if (c->opt.precision >= TNQE_PREC_BF16X3) run_contractions_oz(c, pm, kets, mH, mS, fi);
   else run_contractions(c, pm, kets, mH, mS, fi);
   record_event(c, c->ev[3]);
@@ -1339,6 +1605,13 @@ void finish_matrix_elements(tnqe_ctx* c, const FinishInfo& fi) {
       c->prof[4] += f1;
     }
   }
+  for (const double* f : fi.bs_flops) {
+    double h[4] = {0, 0, 0, 0};
+    CK(cudaMemcpy(h, f, sizeof(h), cudaMemcpyDeviceToHost));
+    c->prof[5] += h[0];
+    c->prof[8] += h[1];
+    c->prof[7] += h[2];
+  }
   for (const auto& r : fi.ev_reads) {
     float ms = 0.f;
     CK(cudaEventElapsedTime(&ms, c->pev[r[0]], c->pev[r[1]]));
@@ -1366,7 +1639,8 @@ std::vector<long long> graph_key(tnqe_ctx* c, const std::vector<std::pair<int, i
   long long cut = 0;
   static_assert(sizeof(double) == sizeof(long long), "");
   std::memcpy(&cut, &c->opt.cutoff, sizeof(cut));
-  std::vector<long long> k{c->generation, c->opt.precision, c->opt.chi_rot, cut, c->opt.renormalize_rotated,
+  std::vector<long long> k{c->generation, c->opt.precision, c->opt.contraction_form, c->opt.chi_rot, cut,
+                           c->opt.renormalize_rotated,
                            c->opt.max_jacobi_sweeps, c->opt.max_spin, c->tune.oz_bn1, c->tune.oz_bn3,
                            c->tune.spmm_bw, (long long)pl.size()};
   for (const auto& p : pl) k.push_back((long long)p.first * 65536 + p.second);
@@ -1553,6 +1827,20 @@ void prepare_mps(tnqe_ctx* c, const double* const* tensors, const int* bond_dims
   // aligned offsets), then one allocation and one copy
   HostPack pk;
   const size_t o_t = pk.add(host), o_off = pk.add(m.off), o_dims = pk.add(m.dims), o_sec = pk.add(m.sec);
+  const BlockTables bt = block_tables(m.mpo, N);
+  std::vector<size_t> o_choff(N + 1), o_chd(N + 1), o_chw(N + 1);
+  for (int b = 0; b <= N; ++b) {
+    o_choff[b] = pk.add(bt.ch_off[b]);
+    o_chd[b] = pk.add(bt.ch_d[b]);
+    o_chw[b] = pk.add(bt.ch_w[b]);
+  }
+  std::vector<size_t> o_rcoff(N), o_rcd(N), o_rcrows(N), o_rcnnz(N);
+  for (int t = 0; t < N; ++t) {
+    o_rcoff[t] = pk.add(bt.rc_off[t]);
+    o_rcd[t] = pk.add(bt.rc_d[t]);
+    o_rcrows[t] = pk.add(bt.rc_rows[t]);
+    o_rcnnz[t] = pk.add(bt.rc_nnz[t]);
+  }
   std::vector<size_t> o_rowptr(N), o_col(N), o_val(N), o_perm(N), o_v32(N), o_vdf(N), o_ent(N);
   for (int t = 0; t < N; ++t) {
     const MpoSite& S = m.mpo.sites[t];
@@ -1593,6 +1881,23 @@ void prepare_mps(tnqe_ctx* c, const double* const* tensors, const int* bond_dims
   m.d_off = reinterpret_cast<long long*>(base + o_off);
   m.d_dims = reinterpret_cast<int*>(base + o_dims);
   m.d_sec = reinterpret_cast<SectorTable*>(base + o_sec);
+  for (int b = 0; b <= N; ++b) {
+    BsChannels ch{};
+    ch.ncls = (int)bt.ch_off[b].size() - 1;
+    ch.off = reinterpret_cast<const int*>(base + o_choff[b]);
+    ch.d = reinterpret_cast<const int*>(base + o_chd[b]);
+    ch.w = reinterpret_cast<const int*>(base + o_chw[b]);
+    m.bs_ch.push_back(ch);
+  }
+  for (int t = 0; t < N; ++t) {
+    BsRows r{};
+    r.ncls = (int)bt.rc_off[t].size() - 1;
+    r.off = reinterpret_cast<const int*>(base + o_rcoff[t]);
+    r.d = reinterpret_cast<const int*>(base + o_rcd[t]);
+    r.rows = reinterpret_cast<const int*>(base + o_rcrows[t]);
+    r.nnz = reinterpret_cast<const int*>(base + o_rcnnz[t]);
+    m.bs_rows.push_back(r);
+  }
   for (int t = 0; t < N; ++t) {
     m.d_rowptr.push_back(reinterpret_cast<int*>(base + o_rowptr[t]));
     m.d_col.push_back(reinterpret_cast<int*>(base + o_col[t]));
@@ -1621,6 +1926,7 @@ void tnqe_default_options(tnqe_options* o) {
   o->cuda_stream = nullptr;
   o->device = 0;
   o->use_graphs = 1;
+  o->contraction_form = TNQE_FORM_BLOCKS;
 }
 
 tnqe_status tnqe_givens_host(const double* V, int N, int* site, int* side, double* c, double* s, int cap,
@@ -1735,6 +2041,8 @@ tnqe_status tnqe_create(const double* h1, const double* eri, int N, int n_alpha,
     c = new tnqe_ctx();
     if (opt) c->opt = *opt; else tnqe_default_options(&c->opt);
     if (c->opt.precision < 0 || c->opt.precision > TNQE_PREC_BF16X15) throw Error(TNQE_ERR_ARG, "unknown precision");
+    if (c->opt.contraction_form != TNQE_FORM_BLOCKS && c->opt.contraction_form != TNQE_FORM_DENSE)
+      throw Error(TNQE_ERR_ARG, "unknown contraction form");
     c->N = N;
     c->na = n_alpha;
     c->nb = n_beta;
@@ -2066,6 +2374,16 @@ tnqe_status tnqe_set_precision(tnqe_ctx* c, int precision) {
     return TNQE_ERR_ARG;
   }
   c->opt.precision = precision;
+  return TNQE_OK;
+}
+
+tnqe_status tnqe_set_form(tnqe_ctx* c, int form) {
+  if (!c) return TNQE_ERR_ARG;
+  if (form != TNQE_FORM_BLOCKS && form != TNQE_FORM_DENSE) {
+    c->err = "unknown contraction form";
+    return TNQE_ERR_ARG;
+  }
+  c->opt.contraction_form = form;
   return TNQE_OK;
 }
 

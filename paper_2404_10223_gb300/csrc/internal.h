@@ -155,6 +155,47 @@ struct SpmmDfDesc {               // Y[a][row][:] = sum val * X[a][col][:] in do
 };
 struct OzGemmDesc;
 
+// block-sparse FP64 contraction (kernels_block.cu).  Every bond index carries a
+// particle-number charge and every MPO channel the charge change of the operator
+// string it carries, so L[a][w][b] can be nonzero only when q(a) = q(b) + d(w),
+// and X, Y likewise.  Only those blocks are computed and read; the arrays keep
+// the dense capacity layout of the dense form ([a][w][b], [a][w][k'][b'],
+// [a][k][w'][b']), so the contraction can be planned before the rotation has
+// decided the ket's sector dimensions.
+struct BsChannels {               // channels of one MPO bond grouped by charge change d(w)
+  int ncls, pad_;
+  const int* off;                 // ncls + 1 offsets into w
+  const int* d;                   // 2 ncls: (d_alpha, d_beta) of each class
+  const int* w;                   // the channel ids, class by class
+};
+struct BsRows {                   // rows k * Dout + w' of one MPO site grouped by d(w') - q(k)
+  int ncls, pad_;
+  const int* off;                 // ncls + 1 offsets into rows
+  const int* d;                   // 2 ncls
+  const int* rows;                // class by class, rows by descending nonzero count
+  const int* nnz;                 // ncls: nonzeros of each class
+};
+struct BsSiteDesc {               // one (pair, site)
+  int Din, Dout, ca, ca2;         // MPO bond dims; bra bond dims
+  int capb, capb2, pad0, pad1;    // ket layout strides (capacities)
+  const double* A;                // bra site [ca][4][ca2]
+  const double* B;                // ket site [capb][4][capb2]
+  const SectorTable* braL;        // bra bonds t, t + 1
+  const SectorTable* braR;
+  const SectorTable* ketL;        // ket bonds t, t + 1 (written by the rotation for rotated kets)
+  const SectorTable* ketR;
+  const double* Lin;              // [ca][Din][capb]
+  double* Lout;                   // [ca2][Dout][capb2]
+  double* X;                      // [ca][Din][4][capb2]
+  double* Y;                      // [ca][4][Dout][capb2]
+  const int* rowptr;              // MPO site CSR (rows k * Dout + w', columns w * 4 + k')
+  const int* col;
+  const double* val;
+  BsChannels chL, chR;            // channel classes of bonds t and t + 1
+  BsRows rows;                    // row classes of site t
+};
+constexpr int BS_MAXRC = 128;      // row classes per MPO site
+
 // status bits written by kernels
 constexpr int STATUS_NOCONV = 1;
 constexpr int STATUS_OVERFLOW = 2;
@@ -188,6 +229,14 @@ int launch_unit_env_f32(float* const* env, int n, void* stream);
 int launch_extract_df(const float2* const* fin, int npairs, double* H, double* S, void* stream);
 int launch_gemm_bf16s(const OzGemmDesc* d, const long long* tile_prefix, int nprob, long long total_tiles,
                       long long max_spin, int* err, int bn, int ns, void* stream);
+// block-sparse FP64 stages; prefix[p] counts the CTAs of the descriptors before p;
+// flops (device, 3 doubles) accumulates the algorithmic FLOPs of stages 1, 2, 3
+int launch_bs_stage1(const BsSiteDesc* d, const long long* prefix, int n, long long total, double* flops,
+                     void* stream);
+int launch_bs_stage2(const BsSiteDesc* d, const long long* prefix, int n, long long total, double* flops,
+                     void* stream);
+int launch_bs_stage3(const BsSiteDesc* d, const long long* prefix, int n, long long total, double* flops,
+                     void* stream);
 int launch_dependence(const double* d_S, int M, double eps, int max_sweeps, double* d_resid, int* d_status,
                       void* stream);
 int launch_solve(const double* d_H, const double* d_S, int M, double eps, int max_sweeps,

@@ -1038,11 +1038,12 @@ int launch_rotate(const RotDesc* d_descs, int npairs, int smem_bytes, void* stre
 // =============================================================================
 // One Givens gate with scratch in a static device array (no allocation).
 //
-// For callers that cannot call cudaMalloc: code running while a stream is
-// being captured into a CUDA graph (where an allocation would end or break
-// the capture), host programs whose device memory is fully reserved up front
-// by their own pool, and host code that must not pay allocation latency
-// inside a time-critical loop.  The caller passes device buffers for the
+// For callers that cannot call cudaMalloc: host programs whose device memory
+// is fully reserved up front by their own pool (a library allocation would
+// fail or fragment it), and host code that must not pay the latency and
+// implicit synchronisation of cudaMalloc / cudaFree inside a time-critical
+// loop.  The call itself synchronises its stream (it reads the result header
+// back).  The caller passes device buffers for the
 // inputs and outputs; all intermediate storage of the step (two-site tensor,
 // SVD blocks, block bookkeeping) lives in tnqe_gate_scratch below, which
 // every GPU that loads this library holds until the process exits.
@@ -1051,6 +1052,8 @@ int launch_rotate(const RotDesc* d_descs, int npairs, int smem_bytes, void* stre
 #include <cstdio>
 #include <cstring>
 #include <mutex>
+
+#include <cuda.h>
 
 #include "../../include/tnqe.h"
 
@@ -1366,19 +1369,42 @@ __global__ void __launch_bounds__(ROT_THREADS) gate_static_kernel(unsigned char*
 constexpr int NA_MAX_DEVICES = 64;
 std::mutex na_mutex;
 void* na_ptr[NA_MAX_DEVICES] = {nullptr};
+CUcontext na_ctx[NA_MAX_DEVICES] = {nullptr};
 
-// Device address of tnqe_gate_scratch on the current device, resolved once per device.
+// The CUDA context current on the calling thread (driver entry point looked up once).
+cudaError_t current_context(CUcontext* out) {
+  static CUresult (*get)(CUcontext*) = nullptr;
+  if (!get) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess) return e;
+    if (q != cudaDriverEntryPointSuccess || !p) return cudaErrorNotSupported;
+    get = reinterpret_cast<CUresult (*)(CUcontext*)>(p);
+  }
+  return get(out) == CUDA_SUCCESS ? cudaSuccess : cudaErrorDeviceUninitialized;
+}
+
+// Device address of tnqe_gate_scratch on the current device.  Set up once per
+// device and context: a device reset gives the device a new primary context
+// (and the module a new load), so the address is looked up again then.
 cudaError_t gate_scratch_ptr(unsigned char** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= NA_MAX_DEVICES) return cudaErrorInvalidDevice;
+  CUcontext ctx = nullptr;
+  e = current_context(&ctx);                               // NULL before the runtime's first use of the device
+  if (e != cudaSuccess) return e;
   std::lock_guard<std::mutex> lock(na_mutex);
-  if (!na_ptr[dev]) {
+  if (!ctx || !na_ptr[dev] || na_ctx[dev] != ctx) {
     void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, tnqe_gate_scratch);
+    e = cudaGetSymbolAddress(&p, tnqe_gate_scratch);      // also makes the primary context current
+    if (e != cudaSuccess) return e;
+    e = current_context(&ctx);
     if (e != cudaSuccess) return e;
     na_ptr[dev] = p;
+    na_ctx[dev] = ctx;
   }
   *out = static_cast<unsigned char*>(na_ptr[dev]);
   return cudaSuccess;

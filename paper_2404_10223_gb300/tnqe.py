@@ -19,6 +19,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libtnqe.so")
 
 TNQE_PREC_FP64, TNQE_PREC_TF32X3, TNQE_PREC_BF16X3, TNQE_PREC_BF16X6, TNQE_PREC_BF16X10, TNQE_PREC_BF16X15 = range(6)
+TNQE_FORM_BLOCKS, TNQE_FORM_DENSE = 0, 1
 TNQE_PROFILE_LEN = 12
 STATUS_NAMES = {0: "TNQE_OK", 1: "TNQE_ERR_ARG", 2: "TNQE_ERR_STATE", 3: "TNQE_ERR_NOMEM", 4: "TNQE_ERR_CUDA",
                 5: "TNQE_ERR_NOCONV", 6: "TNQE_ERR_TIMEOUT", 7: "TNQE_ERR_NUMERIC"}
@@ -34,12 +35,13 @@ class tnqe_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("chi_rot", ctypes.c_int), ("cutoff", ctypes.c_double),
                 ("solve_eps", ctypes.c_double), ("renormalize_rotated", ctypes.c_int),
                 ("max_jacobi_sweeps", ctypes.c_int), ("max_spin", ctypes.c_longlong),
-                ("cuda_stream", ctypes.c_void_p), ("device", ctypes.c_int), ("use_graphs", ctypes.c_int)]
+                ("cuda_stream", ctypes.c_void_p), ("device", ctypes.c_int), ("use_graphs", ctypes.c_int),
+                ("contraction_form", ctypes.c_int)]
 
 
 EXPORTED = ["tnqe_default_options", "tnqe_mpo_host", "tnqe_check_mps", "tnqe_givens_host",
             "tnqe_rotate_integrals_host", "tnqe_gate_host", "tnqe_create", "tnqe_add_mps", "tnqe_reset_mps", "tnqe_rotate",
-            "tnqe_get_rotated", "tnqe_matrix_elements", "tnqe_solve", "tnqe_set_precision", "tnqe_last_timing", "tnqe_last_profile", "tnqe_apply_gate_noalloc",
+            "tnqe_get_rotated", "tnqe_matrix_elements", "tnqe_solve", "tnqe_set_precision", "tnqe_set_form", "tnqe_last_timing", "tnqe_last_profile", "tnqe_apply_gate_noalloc",
             "tnqe_solve_ex", "tnqe_dependence", "tnqe_autotune", "tnqe_set_tuning", "tnqe_clear_graphs", "tnqe_graph_count", "tnqe_last_error",
             "tnqe_destroy"]
 
@@ -69,6 +71,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.tnqe_matrix_elements.argtypes = [P, P, I, P, P]
     lib.tnqe_solve.argtypes = [P, P, P, I, P, P, ctypes.POINTER(I), ctypes.POINTER(D)]
     lib.tnqe_set_precision.argtypes = [P, I]
+    lib.tnqe_set_form.argtypes = [P, I]
     lib.tnqe_last_timing.argtypes = [P, P, ctypes.POINTER(I)]
     lib.tnqe_last_profile.argtypes = [P, P, I]
     lib.tnqe_apply_gate_noalloc.argtypes = [P, P, I, I, I, P, P, P, D, D, I, I, D, I, P, P, P,
@@ -271,6 +274,10 @@ def tnqe_set_precision(ctx, precision: int):
     _check(ctx, load().tnqe_set_precision(ctx, precision))
 
 
+def tnqe_set_form(ctx, form: int):
+    _check(ctx, load().tnqe_set_form(ctx, form))
+
+
 def tnqe_last_timing(ctx):
     t = np.zeros(3)
     n = ctypes.c_int()
@@ -367,6 +374,9 @@ class Context:
 
     def set_precision(self, p: int):
         tnqe_set_precision(self.ctx, p)
+
+    def set_form(self, form: int):
+        tnqe_set_form(self.ctx, form)
 
     def last_timing(self):
         return tnqe_last_timing(self.ctx)

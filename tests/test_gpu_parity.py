@@ -86,9 +86,14 @@ def n10():
     return w, pairs, HB, SB
 
 
-def test_n10_all_pairs_equal_oracle(n10):
+FORMS = [tnqe.TNQE_FORM_BLOCKS, tnqe.TNQE_FORM_DENSE]
+
+
+@pytest.mark.parametrize("form", FORMS)
+def test_n10_all_pairs_equal_oracle(n10, form):
+    """FP64 contraction in charge blocks (default) and over the dense zero-padded tensors."""
     w, pairs, HB, SB = n10
-    with gpu_ctx(w) as g:
+    with gpu_ctx(w, contraction_form=form) as g:
         HG, SG = g.matrix_elements(pairs)
     dH = np.abs(HG - HB).max()
     dS = np.abs(SG - SB).max()
@@ -162,7 +167,8 @@ def test_reflection_identity_and_renormalisation():
     assert abs(SG[k] - om.overlap(w.mps[0].tensors, w.mps[2].tensors)) <= 1e-12
 
 
-def test_shuffled_bonds_and_ragged_dims():
+@pytest.mark.parametrize("form", FORMS)
+def test_shuffled_bonds_and_ragged_dims(form):
     """Bond indices in arbitrary charge order and unequal chi_i, chi_j."""
     rng = np.random.default_rng(21)
     N, na, nb = 8, 4, 3
@@ -173,7 +179,7 @@ def test_shuffled_bonds_and_ragged_dims():
         U = inputs.draw_rotation(rng, N, 0.4)[1]
         states.append((ts, U))
     o = om.Context(h1, eri, N, na, nb)
-    with tnqe.Context(h1, eri, N, na, nb) as g:
+    with tnqe.Context(h1, eri, N, na, nb, contraction_form=form) as g:
         for ts, U in states:
             o.add_mps(ts, U)
             g.add_mps(ts, U)
@@ -184,14 +190,15 @@ def test_shuffled_bonds_and_ragged_dims():
     assert np.abs(SG - SB).max() <= TOL_HS
 
 
-def test_tiny_chains():
-    for N, na, nb in [(1, 1, 0), (2, 1, 1), (3, 2, 1)]:
+@pytest.mark.parametrize("form", FORMS)
+def test_tiny_chains(form):
+    for N, na, nb in [(1, 1, 0), (2, 1, 1), (3, 2, 1), (4, 0, 2), (3, 3, 3)]:
         rng = np.random.default_rng(N)
         h1, eri = inputs.draw_integrals(rng, N, 2)
         states = [inputs.draw_mps(rng, N, na, nb, 4)[0] for _ in range(2)]
         Us = [np.eye(N), inputs.draw_rotation(rng, N, 0.7)[1]]
         HA, SA = of.matrix_elements(h1, eri, na, nb, states, Us, [(0, 0), (0, 1), (1, 1)])
-        with tnqe.Context(h1, eri, N, na, nb, chi_rot=64) as g:
+        with tnqe.Context(h1, eri, N, na, nb, chi_rot=64, contraction_form=form) as g:
             for t, U in zip(states, Us):
                 g.add_mps(t, U)
             HG, SG = g.matrix_elements([(0, 0), (0, 1), (1, 1)])

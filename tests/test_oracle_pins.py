@@ -319,6 +319,37 @@ def test_truncation_closed_form_two_sites():
     assert ts[0].shape[2] == 1
 
 
+def test_renormalised_rotation_keeps_the_input_norm():
+    """renormalize=True (App. A1's rescaling after truncation) restores the input norm.
+
+    The input state has norm 0.7, so a norm / norm^2 slip fails: the plain
+    truncated state has norm^2 = 0.49 - (discarded weight) (each SVD runs at
+    the canonical centre, so the dropped sigma^2 are orthogonal losses), the
+    renormalised one has norm^2 = 0.49 and is parallel to the plain one.
+    """
+    w = inputs.make_workload(6, 3, 3, 12, 2, 8, seed=4)
+    ts = [t.copy() for t in w.mps[1].tensors]
+    ts[-1] = 0.7 * ts[-1]
+    V = w.mps[1].U
+    plain, disc = om.apply_rotation(ts, V, chi_rot=4, cutoff=1e-14)
+    renorm, disc2 = om.apply_rotation(ts, V, chi_rot=4, cutoff=1e-14, renormalize=True)
+    assert disc > 1e-3 and disc == disc2                       # the case truncates
+    n_plain = om.overlap(plain, plain)
+    n_renorm = om.overlap(renorm, renorm)
+    assert abs(n_plain - (0.49 - disc)) < 1e-12
+    assert abs(n_renorm - 0.49) < 1e-12
+    assert abs(om.overlap(renorm, plain) ** 2 - n_renorm * n_plain) < 1e-12
+    # N = 2 closed form: chi = 1 keeps sigma_1 = c^2 of |updown, vac>; renormalised it is the unit vector
+    t = 0.41
+    c, s = math.cos(t), math.sin(t)
+    d = inputs.determinant_mps(2, (0,), (0,))
+    U = np.array([[c, s], [-s, c]])
+    r1, _ = om.apply_rotation(d, U, chi_rot=1, cutoff=1e-14, renormalize=True)
+    p1, _ = om.apply_rotation(d, U, chi_rot=1, cutoff=1e-14)
+    assert abs(om.overlap(p1, p1) - c ** 4) < 1e-14
+    assert abs(om.overlap(r1, r1) - 1.0) < 1e-14
+
+
 def test_identity_rotation_is_plain_overlap():
     w = inputs.make_workload(6, 3, 3, 12, 2, 8, seed=3)
     ctx = om.Context(w.h1, w.eri, 6, 3, 3)

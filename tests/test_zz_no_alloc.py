@@ -1,9 +1,10 @@
 """The allocation-free single-gate entry point against the allocating path.
 
-tnqe_apply_gate_noalloc serves callers that cannot call cudaMalloc (work
-issued during CUDA-graph capture, programs with a pre-reserved device pool,
-latency-critical host loops): it keeps all of its working storage in one
-static device array.  These tests call it through the C ABI and compare what
+tnqe_apply_gate_noalloc serves callers that cannot call cudaMalloc (programs
+whose device memory is all handed out by their own pool reserved at start-up,
+host loops that must not pay the latency and implicit synchronisation of
+cudaMalloc / cudaFree): it keeps all of its working storage in one static
+device array.  These tests call it through the C ABI and compare what
 it produces with the ordinary tnqe_rotate path, on consecutive calls that
 share that static array.  This file is collected last on purpose.
 """
