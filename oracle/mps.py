@@ -167,8 +167,9 @@ def apply_rotation(tensors: Sequence[np.ndarray], V: np.ndarray, chi_rot: int, c
     """Truncated G(V)|MPS> for a left-canonical MPS (centre on the last site).
 
     Returns (new tensors, total discarded weight sum sigma^2).  If ``trace`` is
-    a list, each gate appends ``(k, sigma)``: the kept count and the full
-    singular-value list of its SVD (diagnostics only; the arithmetic is the
+    a list, each gate appends ``(k, sigma, rows)``: the kept count, the full
+    singular-value list of its SVD and, for each kept left singular vector, the
+    row (l, k1) of its largest entry (diagnostics only; the arithmetic is the
     same either way).
     """
     ts = [np.array(t, dtype=float, copy=True) for t in tensors]
@@ -195,7 +196,7 @@ def apply_rotation(tensors: Sequence[np.ndarray], V: np.ndarray, chi_rot: int, c
             k = max(k, 1)
         discarded += float(np.sum(sig[k:] ** 2))
         if trace is not None:
-            trace.append((k, sig.copy()))
+            trace.append((k, sig.copy(), np.argmax(np.abs(u[:, :k]), axis=0)))
         u, sk, vt = u[:, :k], sig[:k], vt[:k]
         if side == "L":
             ts[a] = (u * sk).reshape(chl, 4, k)
