@@ -5,7 +5,11 @@ A step is one tnqe_matrix_elements call over all M(M+1)/2 pairs of the
 workload (rotation of every off-diagonal pair + transfer contraction of every
 pair), with the states already resident in HBM.  Default workload: N = 14
 spatial orbitals, 7 + 7 electrons, L = 28, M = 16 states at chi = 128
-(136 pairs), seeded synthetic inputs.
+(136 pairs), seeded synthetic inputs.  Default form: the FP64 contraction in
+particle-number charge blocks.  The line also times, on the same workload,
+the plain (dense) FP64 GPU form and the sliced-BF16 tensor-core form, and
+compares every form's H, S and lowest energy with the stored oracle values
+(tests/golden/, written by the oracle alone).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
 
@@ -15,6 +19,7 @@ the units of all ranks over the slowest rank's time.
 """
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -33,6 +38,7 @@ PREC = {"fp64": 0, "tf32x3": 1, "bf16x3": 2, "bf16x6": 3, "bf16x10": 4, "bf16x15
 DTYPE = {"fp64": "f64", "tf32x3": "tf32x3", "bf16x3": "bf16x3", "bf16x6": "bf16x6", "bf16x10": "bf16x10",
          "bf16x15": "bf16x15"}
 PRODUCTS = {"bf16x3": 3, "bf16x6": 6, "bf16x10": 10, "bf16x15": 15}   # BF16 slice products per GEMM
+FORMS = {"blocks": 0, "dense": 1}                                      # FP64 contraction form
 
 
 def load_peaks():
@@ -121,54 +127,112 @@ def max_over_ranks(x, world):
     return float(t.item())
 
 
-def oracle_sample(w, seconds_cap=40.0):
-    """The CPU oracle as it stands on a bounded sample of the workload's pairs."""
+def blas_info():
+    """Name and version of the BLAS numpy uses, and the host's core count."""
+    try:
+        d = np.show_config(mode="dicts")["Build Dependencies"]["blas"]
+        name = f"{d.get('name')} {d.get('version')}"
+    except Exception:
+        name = "unknown"
+    threads = os.environ.get("OPENBLAS_NUM_THREADS") or os.environ.get("OMP_NUM_THREADS")
+    return name, int(threads) if threads else os.cpu_count()
+
+
+def oracle_pair_times(w, sample):
+    """Seconds per pair of the CPU oracle as it stands; the MPOs of the sample's bras
+    are built outside the timed region (host planning, as tnqe_add_mps does)."""
     from oracle import mps as om
     o = om.Context(w.h1, w.eri, w.N, w.n_alpha, w.n_beta, cutoff=w.cutoff)
     for m in w.mps:
         o.add_mps(m.tensors, m.U)
-    o.mpo(0)                      # basis-0 operator built outside the timed region (host planning)
-    sample = [(0, 1), (0, 0)]
-    done, t0 = [], time.time()
+    for i in sorted({i for i, _ in sample}):
+        o.mpo(i)
+    out = []
     for p in sample:
+        t0 = time.perf_counter()
         o.pair(*p)
-        done.append(p)
-        if time.time() - t0 > seconds_cap:
-            break
-    el = time.time() - t0
-    return len(done) / el, el, done
+        out.append(time.perf_counter() - t0)
+    return out
 
 
-def cpu_threads():
-    try:
-        from threadpoolctl import threadpool_info
-        n = [i.get("num_threads") for i in threadpool_info() if i.get("user_api") == "blas"]
-        if n:
-            return int(max(n))
-    except Exception:
-        pass
-    return os.cpu_count()
+def oracle_single_thread(workload, pair):
+    """The same oracle pair on one BLAS thread, in a fresh interpreter (the thread count of a
+    BLAS already loaded cannot be lowered)."""
+    code = ("import sys, json, time; sys.path.insert(0, %r); import bench; "
+            "from paper_2404_10223_gb300 import inputs; w = inputs.workload(%r); "
+            "print(json.dumps(bench.oracle_pair_times(w, [%r])))") % (ROOT, workload, tuple(pair))
+    env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=900)
+    if r.returncode != 0:
+        return None
+    return json.loads(r.stdout.strip().splitlines()[-1])[0]
+
+
+def cpu_baseline(w, pairs, single_thread=True):
+    """The oracle on a bounded sample of the workload: one rotated pair (0, 1) and one
+    unrotated pair (1, 1), each timed once, weighted by the workload's mix of rotated and
+    unrotated pairs into the time of one whole step (an extrapolation, labelled as such)."""
+    n_rot = sum(1 for i, j in pairs if i != j)
+    n_unrot = len(pairs) - n_rot
+    t_rot, t_unrot = oracle_pair_times(w, [(0, 1), (1, 1)])
+    step_s = n_rot * t_rot + n_unrot * t_unrot
+    blas, threads = blas_info()
+    out = {"value": len(pairs) / step_s, "unit": UNIT, "cores": threads, "kind": "oracle",
+           "sample": (f"pairs (0,1) rotated {t_rot:.1f} s and (1,1) unrotated {t_unrot:.1f} s of {w.name}, "
+                      f"MPOs of bases 0 and 1 built outside the timed region; value extrapolated to the "
+                      f"step's {n_rot} rotated + {n_unrot} unrotated pairs ({step_s:.0f} s per step)"),
+           "extrapolated": True, "nproc": os.cpu_count(), "blas": blas, "blas_threads": threads,
+           "seconds_per_pair": {"rotated": t_rot, "unrotated": t_unrot}}
+    if single_thread:
+        t1 = oracle_single_thread(w.name, (1, 1))
+        if t1 is not None:
+            out["single_thread"] = {"pair": [1, 1], "seconds": t1, "speedup_of_all_cores": t1 / t_unrot}
+    return out
+
+
+def reference_cycle(w, k):
+    """Pair of reference step k: bra 0 (one MPO, built before the timed steps) against the
+    other states, with the unrotated pair (0, 0) in the workload's share of the steps."""
+    pairs = w.all_pairs()
+    frac = sum(1 for i, j in pairs if i == j) / len(pairs)
+    if math.floor((k + 1) * frac) > math.floor(k * frac):
+        return (0, 0)
+    return (0, 1 + k % (w.M - 1))
 
 
 def run_reference(args):
+    from oracle import mps as om
     from paper_2404_10223_gb300 import inputs
     rank, world, local = dist_init(args.gpus)
     if rank != 0:
         return
     w = inputs.workload(args.workload)
-    times = []
-    for _ in range(args.warmup):
-        oracle_sample(w, 5.0)
-    for _ in range(args.steps):
-        v, el, done = oracle_sample(w, 20.0)
-        times.append(el / len(done))
-    value = 1.0 / statistics.mean(times)
+    o = om.Context(w.h1, w.eri, w.N, w.n_alpha, w.n_beta, cutoff=w.cutoff)
+    for m in w.mps:
+        o.add_mps(m.tensors, m.U)
+    o.mpo(0)                                   # host planning, outside the timed steps
+    for k in range(args.warmup):
+        o.pair(*reference_cycle(w, k))
+    times, done = [], []
+    for k in range(args.steps):
+        p = reference_cycle(w, k)
+        t0 = time.perf_counter()
+        o.pair(*p)
+        times.append(time.perf_counter() - t0)
+        done.append(p)
+    ms = 1000.0 * statistics.mean(times)
+    value = 1000.0 / ms
+    blas, threads = blas_info()
+    n_unrot = sum(1 for p in done if p[0] == p[1])
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * statistics.mean(times) * len(w.all_pairs()),
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": config_of(w, "fp64"),
-            "cpu_baseline": {"kind": "oracle", "value": value, "unit": UNIT, "cores": cpu_threads(),
-                             "sample": "pairs (0,1) and (0,0) of the workload per step, MPO of basis 0 prebuilt"},
+            "cpu_baseline": {"kind": "oracle", "value": value, "unit": UNIT, "cores": threads, "nproc": os.cpu_count(),
+                             "blas": blas,
+                             "sample": (f"one pair of {w.name} per step ({args.steps - n_unrot} rotated, {n_unrot} "
+                                        "unrotated, the workload's mix), bra 0 whose MPO is built before the "
+                                        "timed steps; value = pairs / time of those steps")},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -177,6 +241,30 @@ def config_of(w, prec):
     return {"workload": w.name, "N": w.N, "n_alpha": w.n_alpha, "n_beta": w.n_beta, "M": w.M,
             "pairs": len(w.all_pairs()), "chi": sorted(set(m.chi for m in w.mps)), "seed": w.seed,
             "cutoff": w.cutoff, "precision": prec, "l2": "flushed between steps (256 MiB write)"}
+
+
+def golden(name):
+    path = os.path.join(ROOT, "tests", "golden", f"{name}_oracle.npz")
+    return dict(np.load(path)) if os.path.exists(path) else None
+
+
+def measure_fp64_peak(torch):
+    """FP64 rate of this GPU: cuBLAS DGEMM through torch.matmul (4096^3, best of 3)."""
+    n = 4096
+    a = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    b = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    torch.matmul(a, b)
+    torch.cuda.synchronize()
+    best = float("inf")
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.matmul(a, b)
+        e1.record()
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    del a, b
+    return 2.0 * n ** 3 / (best / 1e3) / 1e12
 
 
 def run_native(args):
@@ -198,9 +286,12 @@ def run_native(args):
     if args.max_pairs > 0:                # a smaller case of the same workload (profiling captures)
         pairs = pairs[:args.max_pairs]
     npairs = len(pairs)
+    gold = golden(w.name) if npairs == len(w.all_pairs()) else None
+    fp64_peak = measure_fp64_peak(torch) if not args.no_fp64_peak else None
     stream = torch.cuda.Stream()
+    form = FORMS[args.form]
     g = tnqe.Context(w.h1, w.eri, w.N, w.n_alpha, w.n_beta, cutoff=w.cutoff, precision=PREC[args.precision],
-                     cuda_stream=stream.cuda_stream, device=local)
+                     contraction_form=form, cuda_stream=stream.cuda_stream, device=local)
     for m in w.mps:
         g.add_mps(m.tensors, m.U)
     tuned = None
@@ -216,94 +307,9 @@ def run_native(args):
     def step():
         g.matrix_elements(pairs, Hd.data_ptr(), Sd.data_ptr())
 
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-    clocks = ClockSampler(local)
-    clocks.start()
-    step_ms, prof = [], np.zeros(tnqe.TNQE_PROFILE_LEN)
-    barrier(world)
-    torch.cuda.synchronize()
-    for _ in range(args.steps):
-        with torch.cuda.stream(stream):
-            flush.fill_(1.0)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        step()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        step_ms.append(e0.elapsed_time(e1))
-        prof += g.last_profile()
-    torch.cuda.synchronize()
-    barrier(world)
-    clk = clocks.stop()
-    replayed = g.graph_count() > 0
-    ms = statistics.mean(step_ms)
-    ms_max = max_over_ranks(ms, world)
-    value = npairs * world / (ms_max / 1000.0)
-    K = args.steps
-    peaks, peak_src = load_peaks()
-    fp64_peak = peaks["bf16_tflops"] * (1.25 / 2250.0)          # nominal FP64 : BF16 dense ratio
-    if args.precision == "fp64":
-        kern = {
-            "rotate_pairs_kernel": (prof[0] / K, prof[4] / K, "alu", fp64_peak, "TFLOP/s"),
-            "gemm_f64_grouped(stage1)": (prof[1] / K, prof[5] / K, "alu", fp64_peak, "TFLOP/s"),
-            "spmm_f64_grouped": (prof[2] / K, prof[6] / K, "hbm", peaks["hbm_gbs"], "GB/s"),
-            "gemm_f64_grouped(stage3)": (prof[3] / K, prof[7] / K, "alu", fp64_peak, "TFLOP/s"),
-        }
-    elif args.precision == "tf32x3":
-        # TF32x3: three TF32 MMAs per product; useful FLOPs against the TF32 dense peak
-        # (measured BF16 burst x nominal TF32:BF16 = 1.1 : 2.25) divided by 3
-        tf32_eff = peaks["bf16_tflops"] * (1.1 / 2.25) / 3.0
-        kern = {
-            "rotate_pairs_kernel": (prof[0] / K, prof[4] / K, "alu", fp64_peak, "TFLOP/s"),
-            "gemm_tf32x3_kernel(stage1)": (prof[1] / K, prof[5] / K, "tensor", tf32_eff, "TFLOP/s"),
-            "spmm_t_f32_kernel": (prof[2] / K, prof[6] / K, "hbm", peaks["hbm_gbs"], "GB/s"),
-            "gemm_tf32x3_kernel(stage3)": (prof[3] / K, prof[7] / K, "tensor", tf32_eff, "TFLOP/s"),
-        }
-    else:
-        # sliced BF16: issued MMA FLOPs (useful x slice products) against the measured BF16 burst peak
-        npr = PRODUCTS[args.precision]
-        kern = {
-            "rotate_pairs_kernel": (prof[0] / K, prof[4] / K, "alu", fp64_peak, "TFLOP/s"),
-            "gemm_bf16s_kernel(stage1)": (prof[1] / K, npr * prof[5] / K, "tensor", peaks["bf16_tflops"], "TFLOP/s"),
-            "spmm_df_kernel": (prof[2] / K, prof[6] / K, "hbm", peaks["hbm_gbs"], "GB/s"),
-            "gemm_bf16s_kernel(stage3)": (prof[3] / K, npr * prof[7] / K, "tensor", peaks["bf16_tflops"], "TFLOP/s"),
-            "slice_rows/cols/sites_kernel": (prof[10] / K, prof[11] / K, "hbm", peaks["hbm_gbs"], "GB/s"),
-        }
-    top = max(kern, key=lambda k: kern[k][0])
-    # DRAM bytes per launch from the ncu captures in profiles/ (read + write), scaled from the
-    # captured case to this launch by the units it processes; None where no capture of the
-    # current kernel exists for this workload.
-    n_rot = sum(1 for i, j in pairs if i != j)
-    # rotate_pairs_kernel: 10.63 MB read + 0.76 MB written by a launch of 2 rotated pairs
-    traffic_table = {("n14_chi128", "rotate_pairs_kernel"): 11.39e6 / 2 * n_rot}
-    traffic = traffic_table.get((w.name, top))
-    t_ms, work, bound, peak, unit = kern[top]
-    achieved = (work / (t_ms / 1e3)) / (1e12 if unit == "TFLOP/s" else 1e9) if t_ms > 0 else 0.0
-    roof = {"kernel": top, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
-            "frac": achieved / peak if peak else None, "traffic": traffic,
-            "peak_source": ({"alu": "FP64 = measured bf16 burst x 1.25/2250 (nominal ratio)",
-                             "tensor": ("TF32x3 useful = measured bf16 burst x 1.1/2.25 / 3"
-                                        if args.precision == "tf32x3" else
-                                        "measured bf16 burst; achieved counts every issued slice product"),
-                             "hbm": f"hbm_gbs ({peak_src})"}[bound]),
-            "ms_per_step": t_ms, "work_per_step": work,
-            "breakdown_ms": {k: v[0] for k, v in kern.items()},
-            "breakdown_scope": ("kernels of the main stream; with the sliced path the (i, i) pairs, which "
-                                "need no rotation, contract on a second stream beside the rotation kernel "
-                                "and are not in the breakdown")}
-    # the plain FP64 form on the same workload, and |dE| of this precision against it
-    Hh = Hd.cpu().numpy().copy()
-    Sh = Sd.cpu().numpy().copy()
-    fp64 = None
-    if args.precision != "fp64" and args.fp64_steps > 0:
-        g.set_precision(0)
-        step()
-        torch.cuda.synchronize()
-        f_ms = []
-        for _ in range(args.fp64_steps):
+    def timed(K, prof=None):
+        out = []
+        for _ in range(K):
             with torch.cuda.stream(stream):
                 flush.fill_(1.0)
             torch.cuda.synchronize()
@@ -312,25 +318,121 @@ def run_native(args):
             step()
             e1.record(stream)
             torch.cuda.synchronize()
-            f_ms.append(e0.elapsed_time(e1))
-        H64 = Hd.cpu().numpy().copy()
-        S64 = Sd.cpu().numpy().copy()
-        g.set_precision(PREC[args.precision])
+            out.append(e0.elapsed_time(e1))
+            if prof is not None:
+                prof += g.last_profile()
+        return out
 
-        def energy(Hv, Sv):
-            Mm = w.M
-            Hm, Sm = np.zeros((Mm, Mm)), np.zeros((Mm, Mm))
-            for (i, j), h, s in zip(pairs, Hv, Sv):
-                Hm[i, j] = Hm[j, i] = h
-                Sm[i, j] = Sm[j, i] = s
-            return g.solve(Hm, Sm)[0][0]
-        e_fast, e_64 = energy(Hh, Sh), energy(H64, S64)
-        f_mean = statistics.mean(f_ms)
-        fp64 = {"value": npairs * world / (max_over_ranks(f_mean, world) / 1000.0), "unit": UNIT,
-                "ms_per_step": f_mean, "steps": args.fp64_steps,
-                "speedup": (max_over_ranks(f_mean, world) / ms_max),
-                "dE_Ha": abs(e_fast - e_64), "E_fp64": e_64,
-                "max_dH": float(np.abs(Hh - H64).max()), "max_dS": float(np.abs(Sh - S64).max())}
+    def energy(Hv, Sv):
+        Hm, Sm = np.zeros((w.M, w.M)), np.zeros((w.M, w.M))
+        for (i, j), h, s_ in zip(pairs, Hv, Sv):
+            Hm[i, j] = Hm[j, i] = h
+            Sm[i, j] = Sm[j, i] = s_
+        return g.solve(Hm, Sm)[0][0]
+
+    def vs_oracle(Hv, Sv):
+        if gold is None:
+            return None
+        return {"dE_Ha": abs(energy(Hv, Sv) - float(gold["E"][0])), "E_oracle": float(gold["E"][0]),
+                "max_dH": float(np.abs(Hv - gold["H"]).max()), "max_dS": float(np.abs(Sv - gold["S"]).max())}
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    prof = np.zeros(tnqe.TNQE_PROFILE_LEN)
+    barrier(world)
+    torch.cuda.synchronize()
+    step_ms = timed(args.steps, prof)
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+    replayed = g.graph_count() > 0
+    ms = statistics.mean(step_ms)
+    ms_max = max_over_ranks(ms, world)
+    value = npairs * world / (ms_max / 1000.0)
+    K = args.steps
+    Hh = Hd.cpu().numpy().copy()
+    Sh = Sd.cpu().numpy().copy()
+    peaks, peak_src = load_peaks()
+    alu_peak = fp64_peak if fp64_peak else peaks["bf16_tflops"] * (1.25 / 2250.0)
+    alu_src = ("measured FP64 rate of this GPU: cuBLAS DGEMM (torch.matmul 4096^3, best of 3) before the timed steps"
+               if fp64_peak else "FP64 = measured bf16 burst x 1.25/2250 (nominal ratio)")
+    rot = ("rotate_pairs_kernel", (prof[0] / K, prof[4] / K, "alu", alu_peak, "TFLOP/s"))
+    if args.precision == "fp64" and form == FORMS["blocks"]:
+        kern = dict([rot,
+                     ("bs_stage1_kernel", (prof[1] / K, prof[5] / K, "alu", alu_peak, "TFLOP/s")),
+                     ("bs_stage2_kernel", (prof[2] / K, prof[8] / K, "alu", alu_peak, "TFLOP/s")),
+                     ("bs_stage3_kernel", (prof[3] / K, prof[7] / K, "alu", alu_peak, "TFLOP/s"))])
+    elif args.precision == "fp64":
+        kern = dict([rot,
+                     ("gemm_f64_grouped(stage1)", (prof[1] / K, prof[5] / K, "alu", alu_peak, "TFLOP/s")),
+                     ("spmm_f64_grouped", (prof[2] / K, prof[6] / K, "hbm", peaks["hbm_gbs"], "GB/s")),
+                     ("gemm_f64_grouped(stage3)", (prof[3] / K, prof[7] / K, "alu", alu_peak, "TFLOP/s"))])
+    elif args.precision == "tf32x3":
+        tf32_eff = peaks["bf16_tflops"] * (1.1 / 2.25) / 3.0
+        kern = dict([rot,
+                     ("gemm_tf32x3_kernel(stage1)", (prof[1] / K, prof[5] / K, "tensor", tf32_eff, "TFLOP/s")),
+                     ("spmm_t_f32_kernel", (prof[2] / K, prof[6] / K, "hbm", peaks["hbm_gbs"], "GB/s")),
+                     ("gemm_tf32x3_kernel(stage3)", (prof[3] / K, prof[7] / K, "tensor", tf32_eff, "TFLOP/s"))])
+    else:
+        npr = PRODUCTS[args.precision]
+        kern = dict([rot,
+                     ("gemm_bf16s_kernel(stage1)", (prof[1] / K, npr * prof[5] / K, "tensor", peaks["bf16_tflops"], "TFLOP/s")),
+                     ("spmm_df_kernel", (prof[2] / K, prof[6] / K, "hbm", peaks["hbm_gbs"], "GB/s")),
+                     ("gemm_bf16s_kernel(stage3)", (prof[3] / K, npr * prof[7] / K, "tensor", peaks["bf16_tflops"], "TFLOP/s")),
+                     ("slice_rows/cols/sites_kernel", (prof[10] / K, prof[11] / K, "hbm", peaks["hbm_gbs"], "GB/s"))])
+    top = max(kern, key=lambda k: kern[k][0])
+    # DRAM bytes per launch from an ncu capture of the current kernel (profiles/), scaled from the
+    # captured case to this launch by the units it processes; None where no capture exists.
+    n_rot = sum(1 for i, j in pairs if i != j)
+    # rotate_pairs_kernel: 10.63 MB read + 0.76 MB written by a launch of 2 rotated pairs of n14_chi128
+    traffic_table = {("n14_chi128", "rotate_pairs_kernel"): 11.39e6 / 2 * n_rot}
+    traffic = traffic_table.get((w.name, top))
+    t_ms, work, bound, peak, unit = kern[top]
+    achieved = (work / (t_ms / 1e3)) / (1e12 if unit == "TFLOP/s" else 1e9) if t_ms > 0 else 0.0
+    roof = {"kernel": top, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+            "frac": achieved / peak if peak else None, "traffic": traffic,
+            "peak_source": {"alu": alu_src,
+                            "tensor": ("TF32x3 useful = measured bf16 burst x 1.1/2.25 / 3"
+                                       if args.precision == "tf32x3" else
+                                       "measured bf16 burst; achieved counts every issued slice product"),
+                            "hbm": f"hbm_gbs ({peak_src})"}[bound],
+            "ms_per_step": t_ms, "work_per_step": work,
+            "work_definition": ("rotation: per gate 2 dL dM dR (two-site blocks) + 8 m n (gate) + 4 m n^2 + "
+                                "8 n^3 per m x n charge block (LAPACK-SVD-equivalent), counted in the kernel"
+                                if top == "rotate_pairs_kernel" else "algorithmic FLOPs of the blocks computed"),
+            "breakdown_ms": {k: v[0] for k, v in kern.items()},
+            "breakdown_scope": ("kernels of the main stream; in the sliced and charge-block forms the (i, i) "
+                                "pairs, which need no rotation, contract on a second stream beside the "
+                                "rotation kernel and are not in the breakdown")}
+    # the other forms on the same workload: the plain (dense) FP64 GPU form and the sliced BF16 form
+    others = {}
+    if args.compare_steps > 0:
+        cfgs = [("plain_fp64_gpu", "fp64", "dense"), ("mixed_precision_bf16x15", "bf16x15", "dense")]
+        for key, prec, fm in cfgs:
+            if (prec, fm) == (args.precision, args.form) or args.compare_steps <= 0:
+                continue
+            g.set_precision(PREC[prec])
+            g.set_form(FORMS[fm])
+            if prec.startswith("bf16") and not args.no_autotune:
+                g.autotune(pairs)
+            step()
+            step()                         # the second identical call captures the graph
+            torch.cuda.synchronize()
+            f_ms = statistics.mean(timed(args.compare_steps))
+            f_max = max_over_ranks(f_ms, world)
+            Hx, Sx = Hd.cpu().numpy().copy(), Sd.cpu().numpy().copy()
+            others[key] = {"value": npairs * world / (f_max / 1000.0), "unit": UNIT, "ms_per_step": f_ms,
+                           "steps": args.compare_steps, "precision": prec, "form": fm,
+                           "headline_speedup": f_max / ms_max, "vs_oracle": vs_oracle(Hx, Sx)}
+        g.set_precision(PREC[args.precision])
+        g.set_form(form)
+        if args.shapes:
+            g.set_tuning(*tuned)
+        elif args.precision.startswith("bf16") and not args.no_autotune:
+            g.autotune(pairs)
     # end to end through host buffers: H2D of every state, D2H of H and S
     pinned = []
     h2d = 0
@@ -346,7 +448,7 @@ def run_native(args):
         g.reset_mps()
         for ts, U in pinned:
             g.add_mps([t.numpy() for t in ts], U.numpy())
-        Hh, Sh = g.matrix_elements(pairs)
+        He, Se = g.matrix_elements(pairs)
         torch.cuda.synchronize()
         if it > 0:
             e2e_ms.append(1000.0 * (time.perf_counter() - t0))
@@ -355,16 +457,15 @@ def run_native(args):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
             "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": DTYPE[args.precision], "data": "synthetic",
-            "config": {**config_of(w, args.precision), "pairs": npairs},
+            "config": {**config_of(w, args.precision), "pairs": npairs, "form": args.form},
             "clocks": clk, "gpu_launches": launches,
             "graph": {"replayed": replayed, "tuned_shapes": tuned},
             "e2e": {"value": e2e_v, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": 16 * npairs},
-            "roofline": roof, "plain_fp64_gpu": fp64}
+            "roofline": roof, "vs_oracle": vs_oracle(Hh, Sh), **others}
+    if "plain_fp64_gpu" in others:
+        line["speedup_vs_plain_fp64_gpu"] = others["plain_fp64_gpu"]["headline_speedup"]
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, el, done = oracle_sample(w, 30.0)
-        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cpu_threads(), "kind": "oracle",
-                                "sample": f"{len(done)} pairs {done} of the workload in {el:.1f} s "
-                                          "(basis-0 MPO built outside the timed region)"}
+        line["cpu_baseline"] = cpu_baseline(w, pairs, single_thread=not args.no_single_thread)
     g.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -377,9 +478,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--workload", default="n14_chi128")
-    ap.add_argument("--precision", default="bf16x15", choices=list(PREC))
-    ap.add_argument("--fp64-steps", type=int, default=2, help="timed steps of the plain FP64 form (0 = skip)")
+    ap.add_argument("--precision", default="fp64", choices=list(PREC))
+    ap.add_argument("--form", default="blocks", choices=list(FORMS),
+                    help="FP64 contraction in charge blocks (default) or dense")
+    ap.add_argument("--compare-steps", type=int, default=2,
+                    help="timed steps of the plain FP64 and sliced-BF16 forms (0 = skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-single-thread", action="store_true", help="skip the one-thread oracle leg")
+    ap.add_argument("--no-fp64-peak", action="store_true", help="skip the DGEMM probe of the FP64 peak")
     ap.add_argument("--max-pairs", type=int, default=0, help="use only the first K pairs (profiling on a small case)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-buffer leg")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes (profiling)")

@@ -263,6 +263,7 @@ tnqe_status tnqe_set_precision(tnqe_ctx* ctx, int precision);
 /* Change the form of the FP64 contraction (tnqe_form) of later calls. */
 tnqe_status tnqe_set_form(tnqe_ctx* ctx, int form);
 
+
 /* Device time (ms) of the phases of the last tnqe_matrix_elements call,
  * measured with CUDA events on the context stream:
  * times[0] rotation, times[1] contraction, times[2] whole call.

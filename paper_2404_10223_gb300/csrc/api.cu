@@ -520,8 +520,8 @@ void run_rotations(tnqe_ctx* c, const std::vector<std::pair<int, int>>& pairs, R
   upload(c, c->rot_desc.p, descs.data(), sizeof(RotDesc) * np);
   record_event(c, c->pev[0]);
   CKL(launch_rotate(c->rot_desc.as<RotDesc>(), np, 0, c->stream));
-  record_event(c, c->pev[1]);
   c->launches += 1;
+  record_event(c, c->pev[1]);
 }
 
 // read back dims / discarded / status of a finished rotation batch

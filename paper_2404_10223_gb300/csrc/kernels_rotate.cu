@@ -121,7 +121,10 @@ __device__ int jacobi_block(double* W, double* Q, int m, int n, int max_sweeps, 
   return noconv;
 }
 
-constexpr int RT_THREADS = 512;
+#ifndef TNQE_ROT_THREADS
+#define TNQE_ROT_THREADS 1024
+#endif
+constexpr int RT_THREADS = TNQE_ROT_THREADS;
 constexpr int RT_WARPS = RT_THREADS / 32;
 constexpr int MAXBLK = 1024;
 #ifndef TNQE_ROT_F32_STOP                    // FP32 sweeps end once gamma^2 / (alpha beta) stays below this
@@ -509,13 +512,20 @@ __device__ int block_svd(const Team& tm, const double* __restrict__ Bm, double* 
 
 // Large SVD blocks run concurrently, one per team of ROT_TEAM_WARPS warps.
 #ifndef TNQE_ROT_TEAMS
-#define TNQE_ROT_TEAMS 4
+#define TNQE_ROT_TEAMS 4                      // teams of RT_WARPS / 4 warps for the large blocks
 #endif
 constexpr int ROT_TEAMS = TNQE_ROT_TEAMS;
 constexpr int ROT_TEAM_WARPS = RT_WARPS / ROT_TEAMS;
 constexpr int ROT_TEAM_THREADS = ROT_TEAM_WARPS * 32;
 static_assert(ROT_TEAMS * ROT_TEAM_WARPS == RT_WARPS, "teams must tile the CTA");
-static_assert(ROT_TEAMS <= 15, "one named barrier per team");
+#ifndef TNQE_ROT_LEAD_WARPS
+#define TNQE_ROT_LEAD_WARPS 8
+#endif
+constexpr int ROT_LEAD_WARPS = TNQE_ROT_LEAD_WARPS;                     // the team of a gate's largest block
+constexpr int ROT_REST_TEAMS = (RT_WARPS - ROT_LEAD_WARPS) / ROT_TEAM_WARPS;
+constexpr int ROT_SLOTS = 1 + ROT_REST_TEAMS + ROT_LEAD_WARPS / ROT_TEAM_WARPS;
+static_assert(ROT_LEAD_WARPS % ROT_TEAM_WARPS == 0 && ROT_LEAD_WARPS <= RT_WARPS, "lead team splits into teams");
+static_assert(ROT_SLOTS <= 15, "one named barrier per team");
 
 __global__ void __launch_bounds__(RT_THREADS) rotate_pairs_kernel(const RotDesc* __restrict__ descs) {
   const RotDesc& D = descs[blockIdx.x];
@@ -531,8 +541,8 @@ __global__ void __launch_bounds__(RT_THREADS) rotate_pairs_kernel(const RotDesc*
   __shared__ unsigned char sig_keep[MAXSIG];
   __shared__ short s_ord[MAXBLK];
   __shared__ int s_nblk, s_nnew, s_total, s_nsig, s_keep, s_status, s_nbig;
-  __shared__ float s_tscr[ROT_TEAMS];
-  __shared__ int s_tbi[ROT_TEAMS], s_next_big, s_next_small;
+  __shared__ float s_tscr[ROT_SLOTS];
+  __shared__ int s_tbi[ROT_SLOTS], s_next_big, s_next_small;
   __shared__ double s_disc, s_red[RT_WARPS], s_flops;
 
   ThetaBlk* tb = reinterpret_cast<ThetaBlk*>(D.meta);
@@ -718,21 +728,21 @@ __global__ void __launch_bounds__(RT_THREADS) rotate_pairs_kernel(const RotDesc*
         ++nb_big;
       }
       s_nbig = nb_big;
-      s_next_big = 0;
+      s_next_big = nb_big > 0 ? 1 : 0;            // block 0, the largest, belongs to the lead team
       s_next_small = 0;
     }
     __syncthreads();
     const int nbig = s_nbig;
     {
-      const int team = warp / ROT_TEAM_WARPS, twarp = warp % ROT_TEAM_WARPS;
-      const SubTeam tm{team * ROT_TEAM_THREADS, ROT_TEAM_THREADS, 1 + team, &s_tscr[team]};
-      const int trk = tm.rank();
-      for (;;) {
-        if (trk == 0) s_tbi[team] = atomicAdd(&s_next_big, 1);
-        tm.sync();
-        const int bi = s_tbi[team];
-        tm.sync();
-        if (bi >= nbig) break;
+      // Large blocks on warp teams.  The largest block of a gate (a quarter to a half
+      // of the gate's SVD work at chi = 128) runs on a lead team of ROT_LEAD_WARPS
+      // warps while the other warps, in teams of ROT_TEAM_WARPS, take the next large
+      // blocks from the counter; the lead team then splits into teams of
+      // ROT_TEAM_WARPS and joins them.  Named barrier 1 is the lead team's, 2.. the
+      // other teams', the split teams' after those.
+      auto run_block = [&](const SubTeam& tm, int bi) {
+        const int trk = tm.rank(), tsz = tm.size();
+        const int w0 = tm.base >> 5, nw = tsz >> 5, twarp = warp - w0;
         const int b = s_ord[bi];
         const NewBlk B = nb[b];
         const bool trans = B.nc > B.nr;
@@ -744,7 +754,7 @@ __global__ void __launch_bounds__(RT_THREADS) rotate_pairs_kernel(const RotDesc*
         double* T = D.tbuf + B.qofs;
         float* Q32 = D.q32 + B.qofs;
         double mx = 0.0;
-        for (int idx = trk; idx < m * n; idx += ROT_TEAM_THREADS) {
+        for (int idx = trk; idx < m * n; idx += tsz) {
           const int wi = idx % m, wj = idx / m;
           const int br = trans ? wj : wi, bc = trans ? wi : wj;
           int k1p = 3, k2p = 3;
@@ -770,15 +780,15 @@ __global__ void __launch_bounds__(RT_THREADS) rotate_pairs_kernel(const RotDesc*
         if (lane == 0) s_red[warp] = mx;
         tm.sync();
         double bmax = 0.0;
-        for (int w2 = 0; w2 < ROT_TEAM_WARPS; ++w2) bmax = fmax(bmax, s_red[team * ROT_TEAM_WARPS + w2]);
+        for (int w2 = 0; w2 < nw; ++w2) bmax = fmax(bmax, s_red[w0 + w2]);
         const double scale = bmax > 0.0 ? bmax : 1.0;
         const double inv = 1.0 / scale;
-        for (int idx = trk; idx < m * n; idx += ROT_TEAM_THREADS) Bm[idx] *= inv;
+        for (int idx = trk; idx < m * n; idx += tsz) Bm[idx] *= inv;
         if (trk == 0) nb[b].scale = scale;
         tm.sync();
         const int ncv = block_svd(tm, Bm, W, Q, W32, Q32, T, m, n, D.max_sweeps);
         if (ncv && trk == 0) atomicOr(&s_status, STATUS_NOCONV | (min(m, 4095) << 8) | (min(n, 4095) << 20));
-        for (int j = twarp; j < n; j += ROT_TEAM_WARPS) {
+        for (int j = twarp; j < n; j += nw) {
           double acc = 0.0;
           for (int u = lane; u < m; u += 32) {
             const double v = W[(size_t)j * m + u];
@@ -787,6 +797,36 @@ __global__ void __launch_bounds__(RT_THREADS) rotate_pairs_kernel(const RotDesc*
           acc = warp_sum(acc);
           if (lane == 0) sig[B.sofs + j] = sqrt(acc) * scale;
         }
+      };
+      int slot, base, nthr, bar;
+      if (warp < ROT_LEAD_WARPS) {
+        slot = 0;
+        base = 0;
+        nthr = ROT_LEAD_WARPS * 32;
+        bar = 1;
+      } else {
+        const int t = (warp - ROT_LEAD_WARPS) / ROT_TEAM_WARPS;
+        slot = 1 + t;
+        base = ROT_LEAD_WARPS * 32 + t * ROT_TEAM_THREADS;
+        nthr = ROT_TEAM_THREADS;
+        bar = 2 + t;
+      }
+      if (slot == 0) {
+        if (nbig > 0) run_block(SubTeam{base, nthr, bar, &s_tscr[slot]}, 0);
+        const int t = warp / ROT_TEAM_WARPS;
+        slot = 1 + ROT_REST_TEAMS + t;
+        base = t * ROT_TEAM_THREADS;
+        nthr = ROT_TEAM_THREADS;
+        bar = 2 + ROT_REST_TEAMS + t;
+      }
+      const SubTeam tm{base, nthr, bar, &s_tscr[slot]};
+      for (;;) {
+        if (tm.rank() == 0) s_tbi[slot] = atomicAdd(&s_next_big, 1);
+        tm.sync();
+        const int bi = s_tbi[slot];
+        tm.sync();
+        if (bi >= nbig) break;
+        run_block(tm, bi);
       }
     }
     const WarpTeam wt;
@@ -1009,6 +1049,8 @@ __global__ void __launch_bounds__(RT_THREADS) rotate_pairs_kernel(const RotDesc*
     *D.flops = s_flops;
   }
 }
+
+
 
 }  // namespace
 
