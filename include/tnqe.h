@@ -165,8 +165,11 @@ tnqe_status tnqe_create(const double* h1, const double* eri, int N, int n_alpha,
  * last site, Eq. A3) to 1e-10, and every bond index must carry a definite
  * (n_alpha, n_beta) charge: A[l,k,r] may be nonzero (above 1e-12 of the
  * site's largest entry) only when q(l) + q(k) = q(r), with the last bond at
- * (n_alpha, n_beta).  Violations return TNQE_ERR_ARG.  Builds the Hamiltonian
- * MPO in basis U on the host and uploads tensors and MPO. */
+ * (n_alpha, n_beta).  Violations return TNQE_ERR_ARG.  Uploads the tensors and
+ * starts the build of the Hamiltonian MPO in basis U on a host thread; the
+ * first tnqe_matrix_elements call with this state as a bra waits for that
+ * build while its rotations run on the GPU, and uploads the MPO (an error of
+ * the build is reported by that call). */
 tnqe_status tnqe_add_mps(tnqe_ctx* ctx, const double* const* tensors, const int* bond_dims,
                          const double* U, int* mps_id);
 

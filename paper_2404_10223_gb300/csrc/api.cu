@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <future>
 #include <map>
 #include <memory>
 #include <stdexcept>
@@ -114,8 +115,11 @@ struct DevMps {
   std::vector<float4*> d_ent;            // (hi, lo, column bits, 0) per MPO nonzero
   std::vector<BsChannels> bs_ch;         // N + 1: channel classes by charge change (device pointers)
   std::vector<BsRows> bs_rows;           // N: MPO rows by charge class (device pointers)
+  std::shared_future<std::shared_ptr<struct MpoPack>> mpo_future;   // the MPO's host build (add_mps)
+  bool mpo_ready = false;                // the MPO is on the device and mpo holds its host copy
   std::vector<void*> owned;
   void free_all() {
+    if (mpo_future.valid()) mpo_future.wait();   // the build reads this state's U
     for (void* p : owned) cudaFree(p);
     owned.clear();
   }
@@ -277,7 +281,7 @@ struct tnqe_ctx {
   // the contraction of the unrotated (diagonal) pairs runs on a second stream,
   // beside the rotation kernel, with its own workspace
   cudaStream_t side = nullptr;
-  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_mpo = nullptr;
   DBuf oz_ws_side, oz_desc_side, split_out, split_idx;
   DBuf con_ws_side, con_desc_side, bs_flops, bs_flops_side;   // block-sparse FP64 form
   bool no_events = false;                  // profiling events off (work on the side stream)
@@ -1482,6 +1486,8 @@ struct SideScope {
   }
 };
 
+void ensure_mpo(tnqe_ctx* c, DevMps& m, cudaStream_t st);
+
 void enqueue_matrix_elements(tnqe_ctx* c, const std::vector<std::pair<int, int>>& pl, double* dH, double* dS,
                              FinishInfo& fi) {
   const int npairs = (int)pl.size();
@@ -1530,6 +1536,27 @@ void enqueue_matrix_elements(tnqe_ctx* c, const std::vector<std::pair<int, int>>
   RotBatch rb;
   run_rotations(c, pm, rb, 1);
   record_event(c, c->ev[1]);
+  // The bra states' MPOs: their host builds started in tnqe_add_mps; the host
+  // waits for them here, while the rotation kernel runs, and uploads them (on
+  // the side stream when the (i, i) pairs contract there).
+  {
+    std::vector<int> bras;
+    for (const auto& p : pl)
+      if (!c->mps[p.first]->mpo_ready) bras.push_back(p.first);
+    std::sort(bras.begin(), bras.end());
+    bras.erase(std::unique(bras.begin(), bras.end()), bras.end());
+    if (!bras.empty()) {
+      if (split) {
+        if (!c->ev_mpo) CK(cudaEventCreateWithFlags(&c->ev_mpo, cudaEventDisableTiming));
+        CK(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
+      }
+      for (int i : bras) ensure_mpo(c, *c->mps[i], split ? c->side : c->stream);
+      if (split) {
+        CK(cudaEventRecord(c->ev_mpo, c->side));
+        CK(cudaStreamWaitEvent(c->stream, c->ev_mpo, 0));
+      }
+    }
+  }
   if (split) {
     // submitted after the rotation kernel, so that its CTAs take their SMs first
     CK(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
@@ -1814,55 +1841,64 @@ void order_mps_host(int N, int na, int nb, const double* const* tensors, const i
   }
 }
 
-void prepare_mps(tnqe_ctx* c, const double* const* tensors, const int* bond_dims, const double* U, DevMps& m) {
-  const int N = c->N;
-  std::vector<double> host;
-  order_mps_host(N, c->na, c->nb, tensors, bond_dims, U, m, host);
-  // Hamiltonian in basis U and its MPO
-  std::vector<double> hU, gU;
-  rotate_integrals(c->h1.data(), c->eri.data(), U, N, hU, gU);
-  m.mpo = build_mpo(hU.data(), gU.data(), N);
-  if (m.mpo.dims[N] != 2) throw Error(TNQE_ERR_STATE, "MPO construction failed");
-  // upload: every array of the state packed into one host buffer (256-byte
-  // aligned offsets), then one allocation and one copy
+// The Hamiltonian MPO of one state's basis, built on a host thread and packed
+// for one upload: the CSR of every site in FP64, FP32 and double-float, the row
+// order by nonzero count, and the charge classes of channels and rows.
+struct MpoPack {
+  Mpo mpo;
+  BlockTables bt;
   HostPack pk;
-  const size_t o_t = pk.add(host), o_off = pk.add(m.off), o_dims = pk.add(m.dims), o_sec = pk.add(m.sec);
-  const BlockTables bt = block_tables(m.mpo, N);
-  std::vector<size_t> o_choff(N + 1), o_chd(N + 1), o_chw(N + 1);
+  std::vector<size_t> o_choff, o_chd, o_chw, o_rcoff, o_rcd, o_rcrows, o_rcnnz;
+  std::vector<size_t> o_rowptr, o_col, o_val, o_perm, o_v32, o_vdf, o_ent;
+};
+
+std::shared_ptr<MpoPack> build_mpo_pack(const double* h1, const double* eri, const std::vector<double>& U, int N) {
+  auto P = std::make_shared<MpoPack>();
+  std::vector<double> hU, gU;
+  rotate_integrals(h1, eri, U.data(), N, hU, gU);
+  P->mpo = build_mpo(hU.data(), gU.data(), N);
+  if (P->mpo.dims[N] != 2) throw Error(TNQE_ERR_STATE, "MPO construction failed");
+  P->bt = block_tables(P->mpo, N);
+  const BlockTables& bt = P->bt;
+  HostPack& pk = P->pk;
+  P->o_choff.resize(N + 1);
+  P->o_chd.resize(N + 1);
+  P->o_chw.resize(N + 1);
   for (int b = 0; b <= N; ++b) {
-    o_choff[b] = pk.add(bt.ch_off[b]);
-    o_chd[b] = pk.add(bt.ch_d[b]);
-    o_chw[b] = pk.add(bt.ch_w[b]);
+    P->o_choff[b] = pk.add(bt.ch_off[b]);
+    P->o_chd[b] = pk.add(bt.ch_d[b]);
+    P->o_chw[b] = pk.add(bt.ch_w[b]);
   }
-  std::vector<size_t> o_rcoff(N), o_rcd(N), o_rcrows(N), o_rcnnz(N);
+  for (auto* v : {&P->o_rcoff, &P->o_rcd, &P->o_rcrows, &P->o_rcnnz, &P->o_rowptr, &P->o_col, &P->o_val, &P->o_perm,
+                  &P->o_v32, &P->o_vdf, &P->o_ent})
+    v->resize(N);
   for (int t = 0; t < N; ++t) {
-    o_rcoff[t] = pk.add(bt.rc_off[t]);
-    o_rcd[t] = pk.add(bt.rc_d[t]);
-    o_rcrows[t] = pk.add(bt.rc_rows[t]);
-    o_rcnnz[t] = pk.add(bt.rc_nnz[t]);
+    P->o_rcoff[t] = pk.add(bt.rc_off[t]);
+    P->o_rcd[t] = pk.add(bt.rc_d[t]);
+    P->o_rcrows[t] = pk.add(bt.rc_rows[t]);
+    P->o_rcnnz[t] = pk.add(bt.rc_nnz[t]);
   }
-  std::vector<size_t> o_rowptr(N), o_col(N), o_val(N), o_perm(N), o_v32(N), o_vdf(N), o_ent(N);
   for (int t = 0; t < N; ++t) {
-    const MpoSite& S = m.mpo.sites[t];
-    o_rowptr[t] = pk.add(S.rowptr);
-    o_col[t] = pk.add(S.col);
-    o_val[t] = pk.add(S.val);
+    const MpoSite& S = P->mpo.sites[t];
+    P->o_rowptr[t] = pk.add(S.rowptr);
+    P->o_col[t] = pk.add(S.col);
+    P->o_val[t] = pk.add(S.val);
     {
       const std::vector<int>& rp = S.rowptr;
       std::vector<int> perm(rp.size() - 1);
       for (size_t r = 0; r < perm.size(); ++r) perm[r] = (int)r;
       std::stable_sort(perm.begin(), perm.end(), [&](int x, int y) { return rp[x + 1] - rp[x] > rp[y + 1] - rp[y]; });
-      o_perm[t] = pk.add(perm);
+      P->o_perm[t] = pk.add(perm);
     }
     std::vector<float> v32(S.val.begin(), S.val.end());
-    o_v32[t] = pk.add(v32);
+    P->o_v32[t] = pk.add(v32);
     std::vector<float2> vdf(v32.size());
     for (size_t e = 0; e < v32.size(); ++e) {
       const double v = S.val[e];
       vdf[e].x = (float)v;
       vdf[e].y = (float)(v - (double)vdf[e].x);
     }
-    o_vdf[t] = pk.add(vdf);
+    P->o_vdf[t] = pk.add(vdf);
     std::vector<float4> ent(vdf.size());
     for (size_t e = 0; e < vdf.size(); ++e) {
       int col = S.col[e];
@@ -1870,8 +1906,19 @@ void prepare_mps(tnqe_ctx* c, const double* const* tensors, const int* bond_dims
       std::memcpy(&cf, &col, sizeof(cf));
       ent[e] = make_float4(vdf[e].x, vdf[e].y, cf, 0.f);
     }
-    o_ent[t] = pk.add(ent);
+    P->o_ent[t] = pk.add(ent);
   }
+  return P;
+}
+
+// Host part of tnqe_add_mps: validate and order the state, upload its tensors
+// (one allocation, one copy) and start the build of its MPO on a host thread.
+void prepare_mps(tnqe_ctx* c, const double* const* tensors, const int* bond_dims, const double* U, DevMps& m) {
+  const int N = c->N;
+  std::vector<double> host;
+  order_mps_host(N, c->na, c->nb, tensors, bond_dims, U, m, host);
+  HostPack pk;
+  const size_t o_t = pk.add(host), o_off = pk.add(m.off), o_dims = pk.add(m.dims), o_sec = pk.add(m.sec);
   void* dev = nullptr;
   CK(cudaMalloc(&dev, pk.h.size()));
   m.owned.push_back(dev);
@@ -1881,32 +1928,57 @@ void prepare_mps(tnqe_ctx* c, const double* const* tensors, const int* bond_dims
   m.d_off = reinterpret_cast<long long*>(base + o_off);
   m.d_dims = reinterpret_cast<int*>(base + o_dims);
   m.d_sec = reinterpret_cast<SectorTable*>(base + o_sec);
+  m.mpo_future = std::async(std::launch::async, build_mpo_pack, c->h1.data(), c->eri.data(), std::cref(m.U), N);
+}
+
+// The MPO of state m on the device: wait for its host build (if still running)
+// and upload it with one asynchronous copy on `st`.
+void ensure_mpo(tnqe_ctx* c, DevMps& m, cudaStream_t st) {
+  if (m.mpo_ready) return;
+  if (c->capturing) throw Error(TNQE_ERR_STATE, "MPO upload inside a graph capture");
+  std::shared_ptr<MpoPack> P;
+  try {
+    P = m.mpo_future.get();
+  } catch (const Error&) {
+    throw;
+  } catch (const std::exception& e) {
+    throw Error(TNQE_ERR_NOMEM, std::string("MPO build failed: ") + e.what());
+  }
+  const int N = c->N;
+  void* dev = nullptr;
+  CK(cudaMalloc(&dev, P->pk.h.size()));
+  m.owned.push_back(dev);
+  CK(cudaMemcpyAsync(dev, P->pk.h.data(), P->pk.h.size(), cudaMemcpyHostToDevice, st));
+  unsigned char* base = static_cast<unsigned char*>(dev);
+  const BlockTables& bt = P->bt;
   for (int b = 0; b <= N; ++b) {
     BsChannels ch{};
     ch.ncls = (int)bt.ch_off[b].size() - 1;
-    ch.off = reinterpret_cast<const int*>(base + o_choff[b]);
-    ch.d = reinterpret_cast<const int*>(base + o_chd[b]);
-    ch.w = reinterpret_cast<const int*>(base + o_chw[b]);
+    ch.off = reinterpret_cast<const int*>(base + P->o_choff[b]);
+    ch.d = reinterpret_cast<const int*>(base + P->o_chd[b]);
+    ch.w = reinterpret_cast<const int*>(base + P->o_chw[b]);
     m.bs_ch.push_back(ch);
   }
   for (int t = 0; t < N; ++t) {
     BsRows r{};
     r.ncls = (int)bt.rc_off[t].size() - 1;
-    r.off = reinterpret_cast<const int*>(base + o_rcoff[t]);
-    r.d = reinterpret_cast<const int*>(base + o_rcd[t]);
-    r.rows = reinterpret_cast<const int*>(base + o_rcrows[t]);
-    r.nnz = reinterpret_cast<const int*>(base + o_rcnnz[t]);
+    r.off = reinterpret_cast<const int*>(base + P->o_rcoff[t]);
+    r.d = reinterpret_cast<const int*>(base + P->o_rcd[t]);
+    r.rows = reinterpret_cast<const int*>(base + P->o_rcrows[t]);
+    r.nnz = reinterpret_cast<const int*>(base + P->o_rcnnz[t]);
     m.bs_rows.push_back(r);
   }
   for (int t = 0; t < N; ++t) {
-    m.d_rowptr.push_back(reinterpret_cast<int*>(base + o_rowptr[t]));
-    m.d_col.push_back(reinterpret_cast<int*>(base + o_col[t]));
-    m.d_val.push_back(reinterpret_cast<double*>(base + o_val[t]));
-    m.d_rowperm.push_back(reinterpret_cast<int*>(base + o_perm[t]));
-    m.d_val32.push_back(reinterpret_cast<float*>(base + o_v32[t]));
-    m.d_valdf.push_back(reinterpret_cast<float2*>(base + o_vdf[t]));
-    m.d_ent.push_back(reinterpret_cast<float4*>(base + o_ent[t]));
+    m.d_rowptr.push_back(reinterpret_cast<int*>(base + P->o_rowptr[t]));
+    m.d_col.push_back(reinterpret_cast<int*>(base + P->o_col[t]));
+    m.d_val.push_back(reinterpret_cast<double*>(base + P->o_val[t]));
+    m.d_rowperm.push_back(reinterpret_cast<int*>(base + P->o_perm[t]));
+    m.d_val32.push_back(reinterpret_cast<float*>(base + P->o_v32[t]));
+    m.d_valdf.push_back(reinterpret_cast<float2*>(base + P->o_vdf[t]));
+    m.d_ent.push_back(reinterpret_cast<float4*>(base + P->o_ent[t]));
   }
+  m.mpo = std::move(P->mpo);
+  m.mpo_ready = true;
 }
 
 }  // namespace
@@ -2428,8 +2500,13 @@ void tnqe_destroy(tnqe_ctx* c) {
   c->oz_desc_side.release();
   c->split_out.release();
   c->split_idx.release();
+  c->con_ws_side.release();
+  c->con_desc_side.release();
+  c->bs_flops.release();
+  c->bs_flops_side.release();
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   if (c->ev_join) cudaEventDestroy(c->ev_join);
+  if (c->ev_mpo) cudaEventDestroy(c->ev_mpo);
   if (c->side) cudaStreamDestroy(c->side);
   c->solve_buf.release();
   c->graphs.clear();
