@@ -298,7 +298,8 @@ def run_native(args):
     if args.shapes:
         tuned = [int(x) for x in args.shapes.split(",")]
         g.set_tuning(*tuned)
-    elif args.precision.startswith("bf16") and not args.no_autotune:
+    elif (args.precision.startswith("bf16") or (args.precision == "fp64" and args.form == "blocks")) \
+            and not args.no_autotune:
         tuned, _ = g.autotune(pairs)      # launch shapes, chosen outside the timed region
     Hd = torch.zeros(npairs, dtype=torch.float64, device="cuda")
     Sd = torch.zeros(npairs, dtype=torch.float64, device="cuda")

@@ -80,6 +80,8 @@ typedef struct {
   int device;               /* CUDA device ordinal */
   int use_graphs;           /* 1: replay repeated tnqe_matrix_elements calls from a captured CUDA graph */
   int contraction_form;     /* tnqe_form: FP64 contraction in charge blocks (default) or dense */
+  const char* autotune_cache; /* file of tuned launch shapes per pair-list class (NULL = none); copied */
+  long long workspace_limit;  /* contraction workspace bytes per wave; 0 = 60 % of free device memory */
 } tnqe_options;
 
 /* Form of the FP64 contraction (TNQE_PREC_FP64; the split-precision modes are dense).
@@ -204,7 +206,10 @@ tnqe_status tnqe_get_rotated(tnqe_ctx* ctx, int* bond_dims, double* tensors, lon
  * (re-uploading their descriptors, then one cudaGraphLaunch).  Adding or
  * resetting states, changing options, or any workspace reallocation drops the
  * graphs.  If the workspace of all pairs does not fit in 60% of free device
- * memory the pairs run in waves, synchronised between waves, and are not
+ * memory (or in options.workspace_limit) the pairs run in waves that reuse the
+ * workspace; in the FP64 charge-block form the waves follow each other in
+ * stream order (no host synchronisation, captured and replayed like one wave),
+ * in the other forms the host synchronises between waves and the call is not
  * captured.  In the BF16X* precisions and the charge-block FP64 form the pairs
  * (i, i), which need no rotation, are contracted on a second stream owned by the context (lowest
  * priority) while the rotation kernel runs on the context's stream; that
@@ -213,16 +218,26 @@ tnqe_status tnqe_get_rotated(tnqe_ctx* ctx, int* bond_dims, double* tensors, lon
 tnqe_status tnqe_matrix_elements(tnqe_ctx* ctx, const int* pairs, int npairs,
                                  double* H_out, double* S_out);
 
-/* Launch-shape autotuner of the sliced-BF16 contraction (BF16X* precisions;
- * a no-op otherwise).  Times the given pair list -- normally the one that
- * will be computed repeatedly -- under three candidate shapes (stage-1 and
- * stage-3 GEMM N tiles of 128 or 64 columns, MPO kernel widths of 8, 4 and 2
- * ket columns per CTA), keeps for each kernel the shape with the smallest
- * summed device time, and drops captured graphs.  Each candidate runs twice
- * (the first run warms allocations).  config (3 ints, may be NULL) gets the
- * chosen (bn1, bn3, spmm_bw); times (9 doubles, may be NULL) gets the
- * per-candidate stage-1, stage-3 and MPO milliseconds. */
+/* Launch-shape autotuner of the contraction: the CTA sizes (64, 128, 256) of
+ * the three charge-block stages (FP64, charge-block form), or the stage-1 and
+ * stage-3 GEMM N tiles (128 or 64 columns) and the MPO kernel width (8, 4, 2
+ * ket columns per CTA) of the sliced BF16X* modes; a no-op for the other forms.
+ * The pair list -- normally the one that will be computed repeatedly -- is
+ * reduced to its class: N (which fixes the MPO bond dimensions), precision,
+ * form and the multiset of (bra bond dimension, ket bond dimension) over its
+ * pairs.  With
+ * options.autotune_cache set, a class found in that file takes its stored
+ * shapes without timing; otherwise three candidates are timed (each run twice,
+ * the first warms allocations), each kernel keeps the shape with the smallest
+ * summed device time, and the result is appended to the file as the line
+ * "tnqe-tune <class> | bs_t1 bs_t2 bs_t3 bn1 bn3 spmm_bw".  Captured graphs
+ * are dropped.  config (3 ints, may be NULL) gets the chosen shapes of the
+ * active form; times (9 doubles, may be NULL) the per-candidate stage-1,
+ * stage-3 and stage-2 milliseconds (zero when the cache supplied the shapes). */
 tnqe_status tnqe_autotune(tnqe_ctx* ctx, const int* pairs, int npairs, int* config, double* times);
+
+/* Set the CTA sizes of the three charge-block stages directly (64, 128 or 256). */
+tnqe_status tnqe_set_block_tuning(tnqe_ctx* ctx, int t1, int t2, int t3);
 
 /* Set the launch shapes directly: bn1, bn3 in {64, 128}; spmm_bw in
  * {0 (largest that fits), 1, 2, 4, 8}. */

@@ -246,7 +246,8 @@ struct FinishInfo {
   std::vector<double> pstat;                  // profile values known at planning time
   int launches = 0;
   bool check_err = false;
-  bool single_wave = true;
+  bool single_wave = true;                    // false: the call synchronised between workspace waves
+  int waves = 1;                              // workspace waves of the largest contraction of the call
   std::vector<const double*> bs_flops;        // device FLOP counters (stages 1, 2, 3) of the block-sparse form
 };
 
@@ -296,7 +297,9 @@ struct tnqe_ctx {
   // launch shapes (tnqe_autotune): sliced GEMM N tiles of stages 1 and 3, MPO kernel width (0 = largest that fits)
   struct Tune {
     int oz_bn1 = 128, oz_bn3 = 128, spmm_bw = 0;
+    int bs_t1 = 128, bs_t2 = 128, bs_t3 = 128;   // CTA sizes of the charge-block stages
   } tune;
+  std::string tune_cache;                   // autotune_cache path ("" = none)
   // last tnqe_rotate result
   int kept_pair_valid = 0;
   std::vector<int> kept_dims;
@@ -582,6 +585,13 @@ void site_events(tnqe_ctx* c, FinishInfo& fi, bool last, const std::vector<std::
   }
 }
 
+// Bytes of contraction workspace one wave may use: 60 % of the free device
+// memory (counting the workspace already held), capped by options.workspace_limit.
+double ws_budget(tnqe_ctx* c, size_t avail) {
+  const double b = 0.6 * (double)avail;
+  return c->opt.workspace_limit > 0 ? std::min(b, (double)c->opt.workspace_limit) : b;
+}
+
 void run_contractions(tnqe_ctx* c, const std::vector<std::pair<int, int>>& pairs, const std::vector<KetView>& kets,
                       double* d_H, double* d_S, FinishInfo& fi) {
   const int N = c->N;
@@ -603,7 +613,7 @@ void run_contractions(tnqe_ctx* c, const std::vector<std::pair<int, int>>& pairs
   }
   size_t freeb = 0, totalb = 0;
   CK(cudaMemGetInfo(&freeb, &totalb));
-  const double budget = 0.6 * (double)(freeb + c->con_ws.cap);
+  const double budget = ws_budget(c, freeb + c->con_ws.cap);
   // waves of pairs whose workspace fits
   size_t p0 = 0;
   while (p0 < (size_t)np) {
@@ -780,6 +790,19 @@ void run_contractions(tnqe_ctx* c, const std::vector<std::pair<int, int>>& pairs
 // CTA per (pair, bra sector, channel class), stage 2 one CTA per (pair, bra
 // index).  Algorithmic FLOPs are counted on the device (the ket's sector
 // dimensions are decided there) and read back when the call has finished.
+// Profiling events of site t of workspace wave w: wave 0 uses the context's
+// per-site slots, later waves slots appended after the slicing events.
+int wave_event(tnqe_ctx* c, int w, int t) {
+  const int N = c->N;
+  const int idx = w == 0 ? 2 + 6 * t : 4 + 6 * N * w + 6 * t;
+  while ((int)c->pev.size() < idx + 6) {
+    cudaEvent_t e = nullptr;
+    CK(cudaEventCreate(&e));
+    c->pev.push_back(e);
+  }
+  return idx;
+}
+
 void run_contractions_bs(tnqe_ctx* c, const std::vector<std::pair<int, int>>& pairs, const std::vector<KetView>& kets,
                          double* d_H, double* d_S, FinishInfo& fi) {
   const int N = c->N;
@@ -802,27 +825,43 @@ void run_contractions_bs(tnqe_ctx* c, const std::vector<std::pair<int, int>>& pa
   CK(cudaMemsetAsync(c->bs_flops.p, 0, 4 * sizeof(double), c->stream));
   double* dfl = c->bs_flops.as<double>();
   fi.bs_flops.push_back(dfl);
+  // waves of pairs whose workspace fits in 60 % of the free memory; the waves
+  // reuse the workspace in stream order, so no host synchronisation is needed
   size_t freeb = 0, totalb = 0;
   CK(cudaMemGetInfo(&freeb, &totalb));
-  const double budget = 0.6 * (double)(freeb + c->con_ws.cap);
-  size_t p0 = 0;
-  while (p0 < (size_t)np) {
-    size_t p1 = p0;
+  const double budget = ws_budget(c, freeb + c->con_ws.cap);
+  std::vector<std::pair<int, int>> waves;
+  double need_max = 0.0;
+  for (int p0 = 0; p0 < np;) {
+    int p1 = p0;
     double need = 0.0;
-    while (p1 < (size_t)np) {
+    while (p1 < np) {
       const double add = 8.0 * (2.0 * envsz[p1] + xsz[p1] + ysz[p1]);
       if (p1 > p0 && need + add > budget) break;
       need += add;
       ++p1;
     }
-    const int nw = (int)(p1 - p0);
-    c->con_ws.ensure((size_t)need + 256);
+    waves.push_back({p0, p1});
+    need_max = std::max(need_max, need);
+    p0 = p1;
+  }
+  c->con_ws.ensure((size_t)need_max + 256);
+  auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  struct WaveLayout {
+    size_t base, od, op1, op2, op3, oe, of;
+    int nw;
+    std::vector<long long> tot1, tot2, tot3;
+  };
+  std::vector<WaveLayout> lay(waves.size());
+  std::vector<unsigned char> host;
+  for (size_t wv = 0; wv < waves.size(); ++wv) {
+    const int p0 = waves[wv].first, nw = waves[wv].second - waves[wv].first;
     std::vector<double*> env0(nw), env1(nw), X(nw), Y(nw);
     {
       double* base = c->con_ws.as<double>();
       long long o = 0;
       for (int w = 0; w < nw; ++w) {
-        const int p = (int)p0 + w;
+        const int p = p0 + w;
         env0[w] = base + o;
         o += envsz[p];
         env1[w] = base + o;
@@ -836,11 +875,15 @@ void run_contractions_bs(tnqe_ctx* c, const std::vector<std::pair<int, int>>& pa
     // descriptors: site-major, pairs inside; CTA prefixes per site and stage
     std::vector<BsSiteDesc> ds((size_t)N * nw);
     std::vector<long long> pre1, pre2, pre3;
-    std::vector<long long> tot1(N), tot2(N), tot3(N);
+    WaveLayout& L = lay[wv];
+    L.nw = nw;
+    L.tot1.resize(N);
+    L.tot2.resize(N);
+    L.tot3.resize(N);
     for (int t = 0; t < N; ++t) {
       long long n1 = 0, n2 = 0, n3 = 0;
       for (int w = 0; w < nw; ++w) {
-        const int p = (int)p0 + w;
+        const int p = p0 + w;
         const DevMps& bi = *c->mps[pairs[p].first];
         const KetView& kv = kets[p];
         BsSiteDesc& d = ds[(size_t)t * nw + w];
@@ -876,56 +919,64 @@ void run_contractions_bs(tnqe_ctx* c, const std::vector<std::pair<int, int>>& pa
       pre1.push_back(n1);
       pre2.push_back(n2);
       pre3.push_back(n3);
-      tot1[t] = n1;
-      tot2[t] = n2;
-      tot3[t] = n3;
+      L.tot1[t] = n1;
+      L.tot2[t] = n2;
+      L.tot3[t] = n3;
     }
-    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
     const size_t bd = ds.size() * sizeof(BsSiteDesc), bp = pre1.size() * 8, bf = (size_t)nw * sizeof(double*);
-    const size_t od = 0, op1 = al(bd), op2 = op1 + al(bp), op3 = op2 + al(bp), oe = op3 + al(bp), of = oe + al(bf);
-    const size_t total = of + al(bf);
-    std::vector<unsigned char> host(total, 0);
-    std::memcpy(host.data() + od, ds.data(), bd);
-    std::memcpy(host.data() + op1, pre1.data(), bp);
-    std::memcpy(host.data() + op2, pre2.data(), bp);
-    std::memcpy(host.data() + op3, pre3.data(), bp);
-    std::memcpy(host.data() + oe, env0.data(), bf);
+    L.base = al(host.size());
+    L.od = 0;
+    L.op1 = al(bd);
+    L.op2 = L.op1 + al(bp);
+    L.op3 = L.op2 + al(bp);
+    L.oe = L.op3 + al(bp);
+    L.of = L.oe + al(bf);
+    host.resize(L.base + L.of + al(bf), 0);
+    unsigned char* h = host.data() + L.base;
+    std::memcpy(h + L.od, ds.data(), bd);
+    std::memcpy(h + L.op1, pre1.data(), bp);
+    std::memcpy(h + L.op2, pre2.data(), bp);
+    std::memcpy(h + L.op3, pre3.data(), bp);
+    std::memcpy(h + L.oe, env0.data(), bf);
     std::vector<const double*> fin(nw);
     for (int w = 0; w < nw; ++w) fin[w] = (N & 1) ? env1[w] : env0[w];
-    std::memcpy(host.data() + of, fin.data(), bf);
-    c->con_desc.ensure(total);
-    unsigned char* dd = c->con_desc.as<unsigned char>();
-    upload(c, dd, host.data(), total);
-    CKL(launch_unit_env_f64(reinterpret_cast<double* const*>(dd + oe), nw, c->stream));   // L_0 = 1
+    std::memcpy(h + L.of, fin.data(), bf);
+  }
+  for (size_t wv = 0; wv < waves.size(); ++wv) wave_event(c, (int)wv, N - 1);   // events exist before any launch
+  c->con_desc.ensure(host.size());
+  upload(c, c->con_desc.p, host.data(), host.size());
+  std::vector<std::array<int, 3>> reads;
+  for (size_t wv = 0; wv < waves.size(); ++wv) {
+    const WaveLayout& L = lay[wv];
+    const int nw = L.nw, p0 = waves[wv].first;
+    unsigned char* dd = c->con_desc.as<unsigned char>() + L.base;
+    CKL(launch_unit_env_f64(reinterpret_cast<double* const*>(dd + L.oe), nw, c->stream));   // L_0 = 1
     c->launches += 1;
-    const BsSiteDesc* dsd = reinterpret_cast<const BsSiteDesc*>(dd + od);
+    const BsSiteDesc* dsd = reinterpret_cast<const BsSiteDesc*>(dd + L.od);
     for (int t = 0; t < N; ++t) {
       const size_t pofs = (size_t)t * (nw + 1);
-      cudaEvent_t* E = &c->pev[2 + 6 * t];
+      const int e = wave_event(c, (int)wv, t);
+      cudaEvent_t* E = &c->pev[e];
       record_event(c, E[0]);
-      CKL(launch_bs_stage1(dsd + (size_t)t * nw, reinterpret_cast<const long long*>(dd + op1) + pofs, nw, tot1[t], dfl,
-                           c->stream));
+      CKL(launch_bs_stage1(dsd + (size_t)t * nw, reinterpret_cast<const long long*>(dd + L.op1) + pofs, nw,
+                           L.tot1[t], dfl, c->tune.bs_t1, c->stream));
       record_event(c, E[1]);
-      CKL(launch_bs_stage2(dsd + (size_t)t * nw, reinterpret_cast<const long long*>(dd + op2) + pofs, nw, tot2[t], dfl,
-                           c->stream));
+      CKL(launch_bs_stage2(dsd + (size_t)t * nw, reinterpret_cast<const long long*>(dd + L.op2) + pofs, nw,
+                           L.tot2[t], dfl, c->tune.bs_t2, c->stream));
       record_event(c, E[2]);
-      CKL(launch_bs_stage3(dsd + (size_t)t * nw, reinterpret_cast<const long long*>(dd + op3) + pofs, nw, tot3[t], dfl,
-                           c->stream));
+      CKL(launch_bs_stage3(dsd + (size_t)t * nw, reinterpret_cast<const long long*>(dd + L.op3) + pofs, nw,
+                           L.tot3[t], dfl, c->tune.bs_t3, c->stream));
       record_event(c, E[3]);
       c->launches += 3;
-    }
-    CKL(launch_extract(reinterpret_cast<const double* const*>(dd + of), nw, d_H + p0, d_S + p0, c->stream));
-    c->launches += 1;
-    std::vector<std::array<int, 3>> reads;
-    for (int t = 0; t < N; ++t) {
-      const int e = 2 + 6 * t;
       reads.push_back({e, e + 1, 1});
       reads.push_back({e + 1, e + 2, 2});
       reads.push_back({e + 2, e + 3, 3});
     }
-    site_events(c, fi, p1 == (size_t)np, reads);
-    p0 = p1;
+    CKL(launch_extract(reinterpret_cast<const double* const*>(dd + L.of), nw, d_H + p0, d_S + p0, c->stream));
+    c->launches += 1;
   }
+  if (!c->no_events) fi.ev_reads.insert(fi.ev_reads.end(), reads.begin(), reads.end());
+  fi.waves = std::max(fi.waves, (int)waves.size());
 }
 
 // ----------------------------------------------------------------------------- split-precision contraction
@@ -979,7 +1030,7 @@ void run_contractions_tc(tnqe_ctx* c, const std::vector<std::pair<int, int>>& pa
   }
   size_t freeb = 0, totalb = 0;
   CK(cudaMemGetInfo(&freeb, &totalb));
-  const double budget = 0.6 * (double)(freeb + c->tc_ws.cap);
+  const double budget = ws_budget(c, freeb + c->tc_ws.cap);
   c->tc_err.ensure(256);
   if (!c->err_preset) CK(cudaMemsetAsync(c->tc_err.p, 0, sizeof(int), c->stream));
   size_t p0 = 0;
@@ -1229,7 +1280,7 @@ void run_contractions_oz(tnqe_ctx* c, const std::vector<std::pair<int, int>>& pa
   }
   size_t freeb = 0, totalb = 0;
   CK(cudaMemGetInfo(&freeb, &totalb));
-  const double budget = 0.6 * (double)(freeb + c->oz_ws.cap);
+  const double budget = ws_budget(c, freeb + c->oz_ws.cap);
   c->tc_err.ensure(256);
   if (!c->err_preset) CK(cudaMemsetAsync(c->tc_err.p, 0, sizeof(int), c->stream));
   int* derr = c->tc_err.as<int>();
@@ -1669,7 +1720,7 @@ std::vector<long long> graph_key(tnqe_ctx* c, const std::vector<std::pair<int, i
   std::vector<long long> k{c->generation, c->opt.precision, c->opt.contraction_form, c->opt.chi_rot, cut,
                            c->opt.renormalize_rotated,
                            c->opt.max_jacobi_sweeps, c->opt.max_spin, c->tune.oz_bn1, c->tune.oz_bn3,
-                           c->tune.spmm_bw, (long long)pl.size()};
+                           c->tune.spmm_bw, c->tune.bs_t1, c->tune.bs_t2, c->tune.bs_t3, (long long)pl.size()};
   for (const auto& p : pl) k.push_back((long long)p.first * 65536 + p.second);
   return k;
 }
@@ -1981,6 +2032,65 @@ void ensure_mpo(tnqe_ctx* c, DevMps& m, cudaStream_t st) {
   m.mpo_ready = true;
 }
 
+// The class of a pair list for the tuning cache: N (which fixes the MPO bond
+// dimensions), precision and form, and the multiset of (bra bond dimension,
+// ket bond dimension) over the pairs (the largest over the bonds of each state).
+std::string tune_key(tnqe_ctx* c, const int* pairs, int npairs) {
+  std::map<std::array<int, 2>, int> cls;
+  const int M = (int)c->mps.size();
+  for (int p = 0; p < npairs; ++p) {
+    const int i = pairs[2 * p], j = pairs[2 * p + 1];
+    if (i < 0 || j < 0 || i >= M || j >= M) throw Error(TNQE_ERR_STATE, "unknown MPS id");
+    const DevMps& a = *c->mps[i];
+    const DevMps& b = *c->mps[j];
+    const int da = *std::max_element(a.dims.begin(), a.dims.end());
+    const int db = *std::max_element(b.dims.begin(), b.dims.end());
+    ++cls[{da, db}];
+  }
+  std::string k = "N=" + std::to_string(c->N) + " prec=" + std::to_string(c->opt.precision) +
+                  " form=" + std::to_string(c->opt.contraction_form);
+  for (const auto& kv : cls)
+    k += " " + std::to_string(kv.first[0]) + "x" + std::to_string(kv.first[1]) + "*" + std::to_string(kv.second);
+  return k;
+}
+
+// One line per tuned class: "tnqe-tune <key> | bs_t1 bs_t2 bs_t3 oz_bn1 oz_bn3 spmm_bw".
+bool tune_cache_lookup(tnqe_ctx* c, const std::string& key) {
+  FILE* f = std::fopen(c->tune_cache.c_str(), "r");
+  if (!f) return false;
+  const std::string head = "tnqe-tune " + key + " |";
+  char buf[8192];
+  bool found = false;
+  while (std::fgets(buf, sizeof(buf), f)) {
+    std::string line(buf);
+    if (line.compare(0, head.size(), head) != 0) continue;
+    int v[6];
+    if (std::sscanf(line.c_str() + head.size(), "%d %d %d %d %d %d", &v[0], &v[1], &v[2], &v[3], &v[4], &v[5]) != 6)
+      continue;
+    const bool ok = (v[0] == 64 || v[0] == 128 || v[0] == 256) && (v[1] == 64 || v[1] == 128 || v[1] == 256) &&
+                    (v[2] == 64 || v[2] == 128 || v[2] == 256) && (v[3] == 64 || v[3] == 128) &&
+                    (v[4] == 64 || v[4] == 128) && v[5] >= 0 && v[5] <= 8 && !(v[5] & (v[5] - 1));
+    if (!ok) continue;
+    c->tune.bs_t1 = v[0];
+    c->tune.bs_t2 = v[1];
+    c->tune.bs_t3 = v[2];
+    c->tune.oz_bn1 = v[3];
+    c->tune.oz_bn3 = v[4];
+    c->tune.spmm_bw = v[5];
+    found = true;                                  // the last matching line wins
+  }
+  std::fclose(f);
+  return found;
+}
+
+void tune_cache_store(tnqe_ctx* c, const std::string& key) {
+  FILE* f = std::fopen(c->tune_cache.c_str(), "a");
+  if (!f) throw Error(TNQE_ERR_ARG, "cannot append to the autotune cache " + c->tune_cache);
+  std::fprintf(f, "tnqe-tune %s | %d %d %d %d %d %d\n", key.c_str(), c->tune.bs_t1, c->tune.bs_t2, c->tune.bs_t3,
+               c->tune.oz_bn1, c->tune.oz_bn3, c->tune.spmm_bw);
+  std::fclose(f);
+}
+
 }  // namespace
 
 // ============================================================================= ABI
@@ -1999,6 +2109,8 @@ void tnqe_default_options(tnqe_options* o) {
   o->device = 0;
   o->use_graphs = 1;
   o->contraction_form = TNQE_FORM_BLOCKS;
+  o->autotune_cache = nullptr;
+  o->workspace_limit = 0;
 }
 
 tnqe_status tnqe_givens_host(const double* V, int N, int* site, int* side, double* c, double* s, int cap,
@@ -2112,6 +2224,8 @@ tnqe_status tnqe_create(const double* h1, const double* eri, int N, int n_alpha,
       throw Error(TNQE_ERR_ARG, "electron counts must be in [0, min(N, 14)]");
     c = new tnqe_ctx();
     if (opt) c->opt = *opt; else tnqe_default_options(&c->opt);
+    if (c->opt.autotune_cache) c->tune_cache = c->opt.autotune_cache;
+    c->opt.autotune_cache = nullptr;                 // the context keeps its own copy
     if (c->opt.precision < 0 || c->opt.precision > TNQE_PREC_BF16X15) throw Error(TNQE_ERR_ARG, "unknown precision");
     if (c->opt.contraction_form != TNQE_FORM_BLOCKS && c->opt.contraction_form != TNQE_FORM_DENSE)
       throw Error(TNQE_ERR_ARG, "unknown contraction form");
@@ -2304,51 +2418,96 @@ tnqe_status tnqe_autotune(tnqe_ctx* c, const int* pairs, int npairs, int* config
   try {
     check_ctx(c);
     if (npairs <= 0 || !pairs) throw Error(TNQE_ERR_ARG, "bad pair list");
-    if (c->opt.precision >= TNQE_PREC_BF16X3) {
-      struct Cand {
-        int bn1, bn3, bw;
-      };
-      const Cand cands[3] = {{128, 128, 8}, {64, 64, 4}, {128, 128, 2}};
-      const int keep_graphs = c->opt.use_graphs;
-      c->opt.use_graphs = 0;
-      std::vector<double> Hh(npairs), Sh(npairs);
-      double t[3][3];
-      tnqe_status st = TNQE_OK;
-      for (int k = 0; k < 3 && st == TNQE_OK; ++k) {
-        c->tune.oz_bn1 = cands[k].bn1;
-        c->tune.oz_bn3 = cands[k].bn3;
-        c->tune.spmm_bw = cands[k].bw;
-        for (int rep = 0; rep < 2 && st == TNQE_OK; ++rep)   // the first run warms allocations and caches
-          st = tnqe_matrix_elements(c, pairs, npairs, Hh.data(), Sh.data());
-        t[k][0] = c->prof[1];
-        t[k][1] = c->prof[3];
-        t[k][2] = c->prof[2];
-        if (times)
-          for (int q = 0; q < 3; ++q) times[3 * k + q] = t[k][q];
+    const bool blocks = c->opt.precision == TNQE_PREC_FP64 && c->opt.contraction_form == TNQE_FORM_BLOCKS;
+    const bool sliced = c->opt.precision >= TNQE_PREC_BF16X3;
+    auto fill_config = [&]() {
+      if (!config) return;
+      if (blocks) {
+        config[0] = c->tune.bs_t1;
+        config[1] = c->tune.bs_t2;
+        config[2] = c->tune.bs_t3;
+      } else {
+        config[0] = c->tune.oz_bn1;
+        config[1] = c->tune.oz_bn3;
+        config[2] = c->tune.spmm_bw;
       }
-      c->opt.use_graphs = keep_graphs;
-      if (st != TNQE_OK) return st;
-      int b1 = 0, b3 = 0, bw = 0;
-      for (int k = 1; k < 3; ++k) {
-        if (t[k][0] < t[b1][0]) b1 = k;
-        if (t[k][1] < t[b3][1]) b3 = k;
-        if (t[k][2] < t[bw][2]) bw = k;
-      }
-      c->tune.oz_bn1 = cands[b1].bn1;
-      c->tune.oz_bn3 = cands[b3].bn3;
-      c->tune.spmm_bw = cands[bw].bw;
-      CK(cudaStreamSynchronize(c->stream));
+    };
+    if (!blocks && !sliced) {
+      fill_config();
+      return TNQE_OK;
+    }
+    const std::string key = tune_key(c, pairs, npairs);
+    if (!c->tune_cache.empty() && tune_cache_lookup(c, key)) {   // this class was tuned before
       clear_graphs(c);
+      fill_config();
+      if (times)
+        for (int q = 0; q < 9; ++q) times[q] = 0.0;
+      return TNQE_OK;
     }
-    if (config) {
-      config[0] = c->tune.oz_bn1;
-      config[1] = c->tune.oz_bn3;
-      config[2] = c->tune.spmm_bw;
+    struct Cand {
+      int a, b, w;
+    };
+    // charge-block stages: CTA sizes; sliced GEMMs: N tiles of stages 1 and 3 and MPO kernel width
+    const Cand bcands[3] = {{64, 64, 64}, {128, 128, 128}, {256, 256, 256}};
+    const Cand ocands[3] = {{128, 128, 8}, {64, 64, 4}, {128, 128, 2}};
+    const Cand* cands = blocks ? bcands : ocands;
+    const int keep_graphs = c->opt.use_graphs;
+    c->opt.use_graphs = 0;
+    std::vector<double> Hh(npairs), Sh(npairs);
+    double t[3][3];
+    tnqe_status st = TNQE_OK;
+    auto apply = [&](const Cand& x) {
+      if (blocks) {
+        c->tune.bs_t1 = x.a;
+        c->tune.bs_t3 = x.b;
+        c->tune.bs_t2 = x.w;
+      } else {
+        c->tune.oz_bn1 = x.a;
+        c->tune.oz_bn3 = x.b;
+        c->tune.spmm_bw = x.w;
+      }
+    };
+    for (int k = 0; k < 3 && st == TNQE_OK; ++k) {
+      apply(cands[k]);
+      for (int rep = 0; rep < 2 && st == TNQE_OK; ++rep)   // the first run warms allocations and caches
+        st = tnqe_matrix_elements(c, pairs, npairs, Hh.data(), Sh.data());
+      t[k][0] = c->prof[1];
+      t[k][1] = c->prof[3];
+      t[k][2] = c->prof[2];
+      if (times)
+        for (int q = 0; q < 3; ++q) times[3 * k + q] = t[k][q];
     }
+    c->opt.use_graphs = keep_graphs;
+    if (st != TNQE_OK) return st;
+    int b1 = 0, b3 = 0, bw = 0;
+    for (int k = 1; k < 3; ++k) {
+      if (t[k][0] < t[b1][0]) b1 = k;
+      if (t[k][1] < t[b3][1]) b3 = k;
+      if (t[k][2] < t[bw][2]) bw = k;
+    }
+    apply(Cand{cands[b1].a, cands[b3].b, cands[bw].w});
+    CK(cudaStreamSynchronize(c->stream));
+    clear_graphs(c);
+    if (!c->tune_cache.empty()) tune_cache_store(c, key);
+    fill_config();
     return TNQE_OK;
   } catch (const Error& e) {
     return fail(c, e);
   }
+}
+
+tnqe_status tnqe_set_block_tuning(tnqe_ctx* c, int t1, int t2, int t3) {
+  if (!c) return TNQE_ERR_ARG;
+  for (int t : {t1, t2, t3})
+    if (t != 64 && t != 128 && t != 256) {
+      c->err = "charge-block stage CTA sizes must be 64, 128 or 256";
+      return TNQE_ERR_ARG;
+    }
+  c->tune.bs_t1 = t1;
+  c->tune.bs_t2 = t2;
+  c->tune.bs_t3 = t3;
+  clear_graphs(c);
+  return TNQE_OK;
 }
 
 tnqe_status tnqe_set_tuning(tnqe_ctx* c, int bn1, int bn3, int spmm_bw) {

@@ -230,13 +230,14 @@ int launch_extract_df(const float2* const* fin, int npairs, double* H, double* S
 int launch_gemm_bf16s(const OzGemmDesc* d, const long long* tile_prefix, int nprob, long long total_tiles,
                       long long max_spin, int* err, int bn, int ns, void* stream);
 // block-sparse FP64 stages; prefix[p] counts the CTAs of the descriptors before p;
-// flops (device, 3 doubles) accumulates the algorithmic FLOPs of stages 1, 2, 3
+// flops (device, 3 doubles) accumulates the algorithmic FLOPs of stages 1, 2, 3;
+// threads: CTA size, 64, 128 or 256
 int launch_bs_stage1(const BsSiteDesc* d, const long long* prefix, int n, long long total, double* flops,
-                     void* stream);
+                     int threads, void* stream);
 int launch_bs_stage2(const BsSiteDesc* d, const long long* prefix, int n, long long total, double* flops,
-                     void* stream);
+                     int threads, void* stream);
 int launch_bs_stage3(const BsSiteDesc* d, const long long* prefix, int n, long long total, double* flops,
-                     void* stream);
+                     int threads, void* stream);
 int launch_dependence(const double* d_S, int M, double eps, int max_sweeps, double* d_resid, int* d_status,
                       void* stream);
 int launch_solve(const double* d_H, const double* d_S, int M, double eps, int max_sweeps,

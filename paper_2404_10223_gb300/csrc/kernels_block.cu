@@ -25,7 +25,6 @@
 namespace tnqe {
 namespace {
 
-constexpr int BS_THREADS = 128;
 constexpr int BS_SMEM = 6144;                 // doubles of staged operand per CTA (48 KiB)
 
 __device__ __forceinline__ int bs_problem(const long long* prefix, int n, long long x) {
@@ -55,6 +54,7 @@ __device__ __forceinline__ int bs_find(const SectorTable* T, int na, int nb) {
 // X[a][w][k'][g] = sum_{b in beta} L[a][w][b] B[b][k'][g] for a in alpha, w in class c,
 // beta = q(alpha) - d(c), g in gamma_k' = beta + q(k').  Where beta is absent from the
 // ket's bond t the block is zero and is written as such (stage 2 reads it).
+template <int BS_THREADS>
 __global__ void __launch_bounds__(BS_THREADS) bs_stage1_kernel(const BsSiteDesc* __restrict__ descs,
                                                               const long long* __restrict__ prefix, int n,
                                                               double* flops) {
@@ -130,6 +130,7 @@ __global__ void __launch_bounds__(BS_THREADS) bs_stage1_kernel(const BsSiteDesc*
 // ----------------------------------------------------------------------------- stage 2
 // Y[a][row][g] = sum_e W_e X[a][col_e][g] for every MPO row (k, w'), g in the ket
 // sector gamma = q(a) - (d(w') - q(k)) of bond t + 1.
+template <int BS_THREADS>
 __global__ void __launch_bounds__(BS_THREADS) bs_stage2_kernel(const BsSiteDesc* __restrict__ descs,
                                                               const long long* __restrict__ prefix, int n,
                                                               double* flops) {
@@ -186,6 +187,7 @@ __global__ void __launch_bounds__(BS_THREADS) bs_stage2_kernel(const BsSiteDesc*
 // L'[a'][w'][g] = sum_k sum_{a in alpha' - q(k)} A[a][k][a'] Y[a][k][w'][g] for a' in
 // alpha', w' in class c', g in beta' = q(alpha') - d(c').  Nothing is written where
 // beta' is absent from the ket's bond t + 1 (no later stage reads it).
+template <int BS_THREADS>
 __global__ void __launch_bounds__(BS_THREADS) bs_stage3_kernel(const BsSiteDesc* __restrict__ descs,
                                                               const long long* __restrict__ prefix, int n,
                                                               double* flops) {
@@ -270,25 +272,30 @@ __global__ void __launch_bounds__(BS_THREADS) bs_stage3_kernel(const BsSiteDesc*
 
 }  // namespace
 
+// CTA sizes of the stages (launch shapes the autotuner chooses from)
+#define BS_LAUNCH(kernel)                                                                                   \
+  do {                                                                                                      \
+    if (total <= 0) return 0;                                                                               \
+    cudaStream_t st = (cudaStream_t)stream;                                                                 \
+    if (threads == 64) kernel<64><<<(unsigned)total, 64, 0, st>>>(d, prefix, n, flops);                     \
+    else if (threads == 256) kernel<256><<<(unsigned)total, 256, 0, st>>>(d, prefix, n, flops);             \
+    else kernel<128><<<(unsigned)total, 128, 0, st>>>(d, prefix, n, flops);                                 \
+    return (int)cudaGetLastError();                                                                         \
+  } while (0)
+
 int launch_bs_stage1(const BsSiteDesc* d, const long long* prefix, int n, long long total, double* flops,
-                     void* stream) {
-  if (total <= 0) return 0;
-  bs_stage1_kernel<<<(unsigned)total, BS_THREADS, 0, (cudaStream_t)stream>>>(d, prefix, n, flops);
-  return (int)cudaGetLastError();
+                     int threads, void* stream) {
+  BS_LAUNCH(bs_stage1_kernel);
 }
 
 int launch_bs_stage2(const BsSiteDesc* d, const long long* prefix, int n, long long total, double* flops,
-                     void* stream) {
-  if (total <= 0) return 0;
-  bs_stage2_kernel<<<(unsigned)total, BS_THREADS, 0, (cudaStream_t)stream>>>(d, prefix, n, flops);
-  return (int)cudaGetLastError();
+                     int threads, void* stream) {
+  BS_LAUNCH(bs_stage2_kernel);
 }
 
 int launch_bs_stage3(const BsSiteDesc* d, const long long* prefix, int n, long long total, double* flops,
-                     void* stream) {
-  if (total <= 0) return 0;
-  bs_stage3_kernel<<<(unsigned)total, BS_THREADS, 0, (cudaStream_t)stream>>>(d, prefix, n, flops);
-  return (int)cudaGetLastError();
+                     int threads, void* stream) {
+  BS_LAUNCH(bs_stage3_kernel);
 }
 
 }  // namespace tnqe

@@ -36,13 +36,14 @@ class tnqe_options(ctypes.Structure):
                 ("solve_eps", ctypes.c_double), ("renormalize_rotated", ctypes.c_int),
                 ("max_jacobi_sweeps", ctypes.c_int), ("max_spin", ctypes.c_longlong),
                 ("cuda_stream", ctypes.c_void_p), ("device", ctypes.c_int), ("use_graphs", ctypes.c_int),
-                ("contraction_form", ctypes.c_int)]
+                ("contraction_form", ctypes.c_int), ("autotune_cache", ctypes.c_char_p),
+                ("workspace_limit", ctypes.c_longlong)]
 
 
 EXPORTED = ["tnqe_default_options", "tnqe_mpo_host", "tnqe_check_mps", "tnqe_givens_host",
             "tnqe_rotate_integrals_host", "tnqe_gate_host", "tnqe_create", "tnqe_add_mps", "tnqe_reset_mps", "tnqe_rotate",
             "tnqe_get_rotated", "tnqe_matrix_elements", "tnqe_solve", "tnqe_set_precision", "tnqe_set_form", "tnqe_last_timing", "tnqe_last_profile", "tnqe_apply_gate_noalloc",
-            "tnqe_solve_ex", "tnqe_dependence", "tnqe_autotune", "tnqe_set_tuning", "tnqe_clear_graphs", "tnqe_graph_count", "tnqe_last_error",
+            "tnqe_solve_ex", "tnqe_dependence", "tnqe_autotune", "tnqe_set_tuning", "tnqe_set_block_tuning", "tnqe_clear_graphs", "tnqe_graph_count", "tnqe_last_error",
             "tnqe_destroy"]
 
 _lib = None
@@ -80,6 +81,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.tnqe_dependence.argtypes = [P, P, I, D, P]
     lib.tnqe_autotune.argtypes = [P, P, I, P, P]
     lib.tnqe_set_tuning.argtypes = [P, I, I, I]
+    lib.tnqe_set_block_tuning.argtypes = [P, I, I, I]
     lib.tnqe_clear_graphs.argtypes = [P]
     lib.tnqe_graph_count.argtypes = [P]
     lib.tnqe_last_error.argtypes = [P]
@@ -292,7 +294,8 @@ def tnqe_last_profile(ctx) -> np.ndarray:
 
 
 def tnqe_autotune(ctx, pairs):
-    """Tune the sliced-BF16 launch shapes on `pairs`; returns ((bn1, bn3, spmm_bw), 3x3 candidate times in ms)."""
+    """Tune the contraction's launch shapes on `pairs` (charge-block CTA sizes, or the sliced-BF16
+    tiles); returns (the three chosen shapes, 3x3 candidate times in ms, zeros from the cache)."""
     pr = np.ascontiguousarray(np.asarray(pairs, dtype=np.int32).reshape(-1, 2))
     cfg = np.zeros(3, dtype=np.int32)
     times = np.zeros(9)
@@ -302,6 +305,10 @@ def tnqe_autotune(ctx, pairs):
 
 def tnqe_set_tuning(ctx, bn1: int, bn3: int, spmm_bw: int):
     _check(ctx, load().tnqe_set_tuning(ctx, bn1, bn3, spmm_bw))
+
+
+def tnqe_set_block_tuning(ctx, t1: int, t2: int, t3: int):
+    _check(ctx, load().tnqe_set_block_tuning(ctx, t1, t2, t3))
 
 
 def tnqe_clear_graphs(ctx):
@@ -344,6 +351,8 @@ class Context:
     def __init__(self, h1, eri, N: int, n_alpha: int, n_beta: int, **opts):
         o = tnqe_default_options()
         for k, v in opts.items():
+            if k == "autotune_cache" and isinstance(v, str):
+                v = v.encode()
             setattr(o, k, v)
         self.N = N
         self.ctx = tnqe_create(h1, eri, N, n_alpha, n_beta, o)
@@ -389,6 +398,9 @@ class Context:
 
     def set_tuning(self, bn1: int, bn3: int, spmm_bw: int):
         tnqe_set_tuning(self.ctx, bn1, bn3, spmm_bw)
+
+    def set_block_tuning(self, t1: int, t2: int, t3: int):
+        tnqe_set_block_tuning(self.ctx, t1, t2, t3)
 
     def clear_graphs(self):
         tnqe_clear_graphs(self.ctx)

@@ -196,3 +196,80 @@ def test_closed_form_determinants_n20():
         hl, sl = lowdin(h1, eri, Us[i], Us[j], oc, oc)
         assert abs(s - sl) <= TOL_HS
         assert abs(h - hl) <= 1e-10 * max(1.0, abs(hl))
+
+
+# ----------------------------------------------------------------------------- N = 20 precision sweep
+# Every contraction mode against the FP64 charge-block form on the states {0, 1, 2, 3} of the
+# N = 20 workload (chi 128, 256, 256, 128; cutoff 1e-10): all 10 pairs among them (6 rotated)
+# and the lowest eigenvalue of their 4 x 4 pencil (E_1 = -387.63 Ha).  Measured on GB300
+# (max|dH|, max|dS|, |dE|):
+#   TF32X3  1.0e-2 / 2.4e-5 / 8.5e-4     BF16X3  1.9e-1 / 1.3e-3 / 3.0e-1
+#   BF16X6  1.5e-4 / 3.4e-7 / 8.1e-5     BF16X10 3.4e-6 / 2.3e-8 / 5.1e-6
+#   BF16X15 4.2e-7 / 3.6e-9 / 4.7e-7
+# The bounds keep a margin of about five over those numbers.
+N20_MODE_BOUNDS = {
+    tnqe.TNQE_PREC_TF32X3: (5e-2, 1.2e-4, 4e-3),
+    tnqe.TNQE_PREC_BF16X3: (1.0, 7e-3, 1.5),
+    tnqe.TNQE_PREC_BF16X6: (7.5e-4, 1.7e-6, 4e-4),
+    tnqe.TNQE_PREC_BF16X10: (1.7e-5, 1.2e-7, 2.5e-5),
+    tnqe.TNQE_PREC_BF16X15: (2e-6, 1.8e-8, 2.4e-6),
+}
+
+
+def test_n20_precision_modes_against_fp64():
+    w = inputs.workload("n20_mixed")
+    states = [0, 1, 2, 3]
+    pairs = [(i, j) for a, i in enumerate(states) for j in states[a:]]
+    with tnqe.Context(w.h1, w.eri, w.N, w.n_alpha, w.n_beta, cutoff=w.cutoff) as g:
+        for k in states:
+            g.add_mps(w.mps[k].tensors, w.mps[k].U)
+        H0, S0 = g.matrix_elements(pairs)
+        E0 = g.solve(*_assemble(len(states), pairs, H0, S0))[0]
+        rows = []
+        for prec, (bh, bs, be) in N20_MODE_BOUNDS.items():
+            g.set_precision(prec)
+            Hv, Sv = g.matrix_elements(pairs)
+            E = g.solve(*_assemble(len(states), pairs, Hv, Sv))[0]
+            dH, dS, dE = np.abs(Hv - H0).max(), np.abs(Sv - S0).max(), abs(E[0] - E0[0])
+            rows.append((prec, dH, dS, dE))
+            print(f"N=20 precision {prec}: max|dH| {dH:.2e}  max|dS| {dS:.2e}  |dE| {dE:.2e}  (E0 {E0[0]:.6f})")
+        for prec, dH, dS, dE in rows:
+            bh, bs, be = N20_MODE_BOUNDS[prec]
+            assert dH <= bh and dS <= bs and dE <= be, (prec, dH, dS, dE)
+
+
+def test_ill_conditioned_pencil_near_duplicate_states():
+    """S with condition number ~1e8 (Sec. IV C): two states plus near-duplicates of them (the last
+    site tensor perturbed by 3e-4 relative, renormalised, same basis).  The GPU solve keeps the same
+    rank as the oracle's canonical orthogonalisation on the same pencil, and agrees on E_1."""
+    w = inputs.workload("n20_mixed")
+    rng = np.random.default_rng(20)
+    base = [0, 3]
+    tens = [w.mps[k].tensors for k in base]
+    Us = [w.mps[k].U for k in base]
+    for k in base:
+        ts = [t.copy() for t in w.mps[k].tensors]
+        last = ts[-1]
+        mask = last != 0.0
+        pert = np.where(mask, rng.normal(size=last.shape), 0.0)
+        ts[-1] = last + 3e-4 * np.linalg.norm(last) * pert / np.linalg.norm(pert)
+        ts[-1] = ts[-1] / np.linalg.norm(ts[-1])
+        tens.append(ts)
+        Us.append(w.mps[k].U)
+    M = len(tens)
+    pairs = [(i, j) for i in range(M) for j in range(i, M)]
+    with tnqe.Context(w.h1, w.eri, w.N, w.n_alpha, w.n_beta, cutoff=w.cutoff) as g:
+        for ts, U in zip(tens, Us):
+            g.add_mps(ts, U)
+        Hv, Sv = g.matrix_elements(pairs)
+        H, S = _assemble(M, pairs, Hv, Sv)
+        EG, CG, rG, kG = g.solve(H, S)
+    lam = np.linalg.eigvalsh(S)
+    cond = lam[-1] / lam[0]
+    EO, CO, rO, kO = om.solve(H, S)
+    print(f"near-duplicate pencil: cond(S) {cond:.2e}, rank GPU {rG} oracle {rO}, E1 GPU {EG[0]:.10f} "
+          f"oracle {EO[0]:.10f}, kappa1 {kG:.3e}")
+    assert 1e7 <= cond <= 1e9
+    assert rG == rO
+    # both solves of the same pencil: rounding amplified by cond(S) (measured 1.6e-8 relative at 1e9)
+    assert abs(EG[0] - EO[0]) <= 1e-7 * max(1.0, abs(EO[0]))

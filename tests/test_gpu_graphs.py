@@ -127,3 +127,58 @@ def test_autotune_and_manual_shapes_give_identical_results():
         with pytest.raises(tnqe.TnqeError):
             g.set_tuning(96, 128, 8)
     assert np.array_equal(H1, H0) and np.array_equal(S1, S0)
+
+
+def test_multi_wave_call_is_captured_and_replayed():
+    """With a workspace limit that splits the pairs into several waves, the charge-block FP64 form runs
+    the waves in stream order without host synchronisation: the call is captured, and eager, captured
+    and replayed results equal the single-wave results bit for bit."""
+    w = inputs.workload("n10_chi32")
+    pairs = w.all_pairs()
+    with ctx_for(w, use_graphs=0) as e:
+        He, Se = e.matrix_elements(pairs)
+    # one pair's workspace at n10_chi32 is a few MB: 40 MB gives several waves
+    with ctx_for(w, use_graphs=1, workspace_limit=40 << 20) as g:
+        outs = [g.matrix_elements(pairs) for _ in range(4)]
+        assert g.graph_count() == 1
+        prof = g.last_profile()
+    for H, S in outs:
+        assert np.array_equal(H, He) and np.array_equal(S, Se)
+    assert prof[1] > 0 and prof[2] > 0 and prof[3] > 0
+
+
+def test_block_stage_cta_sizes_give_identical_results():
+    """The charge-block stages' CTA size changes only the launch shape, never a summation order."""
+    w = inputs.workload("n10_chi32")
+    pairs = w.all_pairs()
+    res = []
+    with ctx_for(w) as g:
+        for t in (64, 128, 256):
+            g.set_block_tuning(t, t, t)
+            res.append(g.matrix_elements(pairs))
+    for H, S in res[1:]:
+        assert np.array_equal(H, res[0][0]) and np.array_equal(S, res[0][1])
+
+
+def test_autotune_cache_file(tmp_path):
+    """tnqe_autotune times the candidates once per pair-list class and stores the choice; a new context
+    with the same cache file takes the stored shapes without timing."""
+    w = inputs.workload("n10_chi32")
+    pairs = w.all_pairs()
+    path = str(tmp_path / "tune.txt")
+    with ctx_for(w, autotune_cache=path) as g:
+        cfg1, times1 = g.autotune(pairs)
+        H1, S1 = g.matrix_elements(pairs)
+    assert all(c in (64, 128, 256) for c in cfg1) and times1.max() > 0
+    lines = open(path).read().splitlines()
+    assert len(lines) == 1 and lines[0].startswith("tnqe-tune N=10 prec=0 form=0 ")
+    with ctx_for(w, autotune_cache=path) as g:
+        cfg2, times2 = g.autotune(pairs)
+        H2, S2 = g.matrix_elements(pairs)
+    assert cfg2 == cfg1 and times2.max() == 0.0
+    assert len(open(path).read().splitlines()) == 1
+    assert np.array_equal(H1, H2) and np.array_equal(S1, S2)
+    # another class (a different pair list) is tuned and appended
+    with ctx_for(w, autotune_cache=path) as g:
+        g.autotune(pairs[:5])
+    assert len(open(path).read().splitlines()) == 2
