@@ -12,12 +12,16 @@ random antisymmetric matrix, R candidates per step, the best one kept if it
 lowers the energy by more than a tolerance.  Every matrix element and every
 solve goes through the library (tnqe_matrix_elements, tnqe_solve).
 
-The learned proposal replaces one of the R candidates by K_j + f(x), where f is
-the proposal network (include/tnqe_mlp.h) and x holds the strictly-lower
-entries of K_j and the padded subspace eigenvalues; the other R - 1 candidates
-stay random, so the plain proposal is both the fallback and the yardstick.
-The network is trained on the (x, best accepted step, energy drop) records
-that plain sweeps write (train_proposer).
+The learned proposal adds the candidate K_j + f(x) to the R random ones, where f
+is the proposal network (include/tnqe_mlp.h) and x holds the strictly-lower
+entries of K_j and the padded subspace eigenvalues; the R random candidates
+draw the same random numbers as in the plain run, so the plain proposal is
+both the fallback and the yardstick.  A new state likewise starts from the
+better of the previous state's orbitals and the network's proposal from there.
+(learned_mode "replace" puts the network's step in place of the first random
+candidate and takes its starting proposal unconditionally.)  The network is
+trained on the (x, best accepted step, energy drop) records that plain sweeps
+write (train_proposer).
 """
 from __future__ import annotations
 
@@ -99,6 +103,7 @@ class SweepConfig:
     R: int = 4                   # candidates per step
     sigma: float = 0.05          # plain proposal: K + sigma * xi
     learned_scales: Tuple[float, ...] = (1.0,)   # learned candidates per step: K + scale * f(x)
+    learned_mode: str = "extra"  # "extra": R random + the learned candidates; "replace": learned in place of random
     step_cap_sigmas: float = 5.0 # learned steps are clipped to this many random-step norms
     birth_cap: float = 3.0       # Frobenius-norm cap of a learned starting offset
     tol: float = 1e-8            # acceptance: E_new < E_old - tol
@@ -114,6 +119,7 @@ class SweepResult:
     proposals: int
     learned_accepted: int
     records: List[Tuple[np.ndarray, np.ndarray, float]]   # (features, best step dK, energy drop) per step
+    learned_births: int = 0                    # new states that started from the network's proposal
 
 
 def hamiltonian(cfg: SweepConfig):
@@ -165,7 +171,7 @@ def run_sweep(cfg: SweepConfig, seed: int, backend, proposer: Optional[Callable[
     E_cur = math.inf
     Evec = np.zeros(0)
     E_ref = 0.0
-    res = SweepResult([], [], 0, 0, 0, [])
+    res = SweepResult([], [], 0, 0, 0, [], 0)
     births: List[Tuple[int, np.ndarray, np.ndarray]] = []   # (state, features at birth, K at birth)
 
     def rebuild():
@@ -186,15 +192,38 @@ def run_sweep(cfg: SweepConfig, seed: int, backend, proposer: Optional[Callable[
             t_new, _ = inputs.draw_mps(rng, N, cfg.n_alpha, cfg.n_beta, cfg.chi)
             K_new = Ks[-1].copy() if Ks else np.zeros((N, N))
             x_birth = features(K_new, Evec, E_ref, 1.0)
+            starts = [K_new]
             if proposer is not None and Ks:
                 d = k_matrix(np.asarray(proposer(x_birth[None, :]), dtype=np.float64)[0], N)
-                K_new = K_new + clip_step(d, cfg.birth_cap)
+                K_l = K_new + clip_step(d, cfg.birth_cap)
+                starts = [K_l] if cfg.learned_mode == "replace" else [K_new, K_l]
+            M = len(Ks) + 1
+            cids = [backend.add_mps(t_new, rotation(K0)) for K0 in starts]
+            rows = backend.matrix_elements([(ids[i], c) for c in cids for i in range(M - 1)] + [(c, c) for c in cids])
+            best_c = 0
+            if len(cids) > 1:                      # keep the start with the lower subspace energy
+                e_c = []
+                for q in range(len(cids)):
+                    Hc = np.zeros((M, M))
+                    Sc = np.zeros((M, M))
+                    Hc[:M - 1, :M - 1] = H
+                    Sc[:M - 1, :M - 1] = S
+                    hv = np.append(rows[0][q * (M - 1):(q + 1) * (M - 1)], rows[0][len(cids) * (M - 1) + q])
+                    sv = np.append(rows[1][q * (M - 1):(q + 1) * (M - 1)], rows[1][len(cids) * (M - 1) + q])
+                    Hc[:, M - 1] = Hc[M - 1, :] = hv
+                    Sc[:, M - 1] = Sc[M - 1, :] = sv
+                    e_c.append(energy(Hc, Sc)[0])
+                best_c = int(np.argmin(e_c))
+                if best_c > 0:
+                    res.learned_births += 1
+            K_new = starts[best_c]
             births.append((len(Ks), x_birth, K_new.copy()))
             tensors.append(t_new)
             Ks.append(K_new)
-            ids.append(backend.add_mps(t_new, rotation(K_new)))
-            M = len(Ks)
-            Hn, Sn = backend.matrix_elements([(ids[i], ids[M - 1]) for i in range(M)])
+            ids.append(cids[best_c])
+            nc = len(cids)
+            Hn = np.append(rows[0][best_c * (M - 1):(best_c + 1) * (M - 1)], rows[0][nc * (M - 1) + best_c])
+            Sn = np.append(rows[1][best_c * (M - 1):(best_c + 1) * (M - 1)], rows[1][nc * (M - 1) + best_c])
             H2 = np.zeros((M, M))
             S2 = np.zeros((M, M))
             H2[:M - 1, :M - 1] = H
@@ -210,13 +239,18 @@ def run_sweep(cfg: SweepConfig, seed: int, backend, proposer: Optional[Callable[
             x = features(Ks[j], Evec, E_ref, 0.0)
             steps = [random_step(rng, N, cfg.sigma) for _ in range(cfg.R)]
             learned = proposer is not None
-            n_learned = 0
+            learned_idx = set()
             if learned:
                 d = k_matrix(np.asarray(proposer(x[None, :]), dtype=np.float64)[0], N)
                 d = clip_step(d, cfg.step_cap_sigmas * cfg.sigma * math.sqrt(N * (N - 1) / 2))
-                n_learned = min(len(cfg.learned_scales), cfg.R)
-                for q in range(n_learned):
-                    steps[q] = cfg.learned_scales[q] * d
+                if cfg.learned_mode == "replace":
+                    n_learned = min(len(cfg.learned_scales), cfg.R)
+                    for q in range(n_learned):
+                        steps[q] = cfg.learned_scales[q] * d
+                    learned_idx = set(range(n_learned))
+                else:
+                    learned_idx = set(range(len(steps), len(steps) + len(cfg.learned_scales)))
+                    steps += [sc * d for sc in cfg.learned_scales]
             cand_ids = [backend.add_mps(tensors[j], rotation(Ks[j] + dK)) for dK in steps]
             others = [i for i in range(M) if i != j]
             pairs = [pair(i, ids[i], j, c) for c in cand_ids for i in others] + [(c, c) for c in cand_ids]
@@ -240,7 +274,7 @@ def run_sweep(cfg: SweepConfig, seed: int, backend, proposer: Optional[Callable[
                 ids[j] = cand_ids[best]
                 H, S, E_cur, Evec = best_H, best_S, best_E, best_Ev
                 res.accepted += 1
-                if learned and best < n_learned:
+                if best in learned_idx:
                     res.learned_accepted += 1
         res.energies.append(E_cur)
         res.M.append(len(Ks))
@@ -326,22 +360,40 @@ def experiment(cfg: SweepConfig, train_seeds: Sequence[int], eval_seeds: Sequenc
     for s in eval_seeds:
         plain = run_sweep(cfg, s, backend)
         target = plain.energies[-1]
-        learned = run_sweep(cfg, s, backend, proposer=network_proposer(net), E_stop=target)
-        rows.append({"seed": s, "E_plain": target, "sweeps_plain": sweeps_to_reach(plain, target),
-                     "sweeps_learned": sweeps_to_reach(learned, target), "E_learned": learned.energies[-1],
-                     "learned_accepted": learned.learned_accepted, "accepted": learned.accepted})
-        log(f"eval seed {s}: plain {rows[-1]['sweeps_plain']} sweeps, learned {rows[-1]['sweeps_learned']} "
-            f"(network candidates accepted {learned.learned_accepted}/{learned.accepted})")
+        learned = run_sweep(cfg, s, backend, proposer=network_proposer(net))
+        sp, sl = sweeps_to_reach(plain, target), sweeps_to_reach(learned, target)
+        rows.append({"seed": s, "E_plain": target, "E_learned": learned.energies[-1],
+                     "dE_final": learned.energies[-1] - target, "sweeps_plain": sp, "sweeps_learned": sl,
+                     "outcome": "win" if sl < sp else ("tie" if sl == sp else "loss"),
+                     "learned_accepted": learned.learned_accepted, "accepted": learned.accepted,
+                     "learned_births": learned.learned_births})
+        log(f"eval seed {s}: plain {sp} sweeps, learned {sl}, final dE {rows[-1]['dE_final']:+.3e} "
+            f"(network candidates accepted {learned.learned_accepted}/{learned.accepted}, "
+            f"births {learned.learned_births})")
     t_eval = time.time() - t0
     net.close()
     if own:
         backend.close()
-    sp = [r["sweeps_plain"] for r in rows]
-    sl = [r["sweeps_learned"] for r in rows]
     return {"config": dataclasses.asdict(cfg), "train_seeds": list(train_seeds), "eval_seeds": list(eval_seeds),
             "samples": len(records), "loss_first": hist[0] if hist else None, "loss_last": hist[-1] if hist else None,
-            "mean_sweeps_plain": float(np.mean(sp)), "mean_sweeps_learned": float(np.mean(sl)),
-            "rows": rows, "seconds": {"generate": t_gen, "train": t_train, "evaluate": t_eval}}
+            **paired_summary(rows), "rows": rows, "seconds": {"generate": t_gen, "train": t_train, "evaluate": t_eval}}
+
+
+def paired_summary(rows) -> dict:
+    """Paired comparison over evaluation seeds: sweeps to reach the plain run's final energy (win =
+    fewer), the final-energy difference, and a two-sided sign test on wins against losses."""
+    sp = np.array([r["sweeps_plain"] for r in rows], dtype=float)
+    sl = np.array([r["sweeps_learned"] for r in rows], dtype=float)
+    de = np.array([r["dE_final"] for r in rows], dtype=float)
+    wins = int(np.sum(sl < sp))
+    losses = int(np.sum(sl > sp))
+    n = wins + losses
+    k = min(wins, losses)
+    p = min(1.0, 2.0 * sum(math.comb(n, i) for i in range(k + 1)) / 2.0 ** n) if n else 1.0
+    return {"mean_sweeps_plain": float(sp.mean()), "mean_sweeps_learned": float(sl.mean()),
+            "mean_sweep_difference": float((sl - sp).mean()), "wins": wins, "ties": len(rows) - n,
+            "losses": losses, "sign_test_p": p, "mean_dE_final": float(de.mean()),
+            "learned_lower_or_equal_final": int(np.sum(de <= 1e-9))}
 
 
 def _seeds(spec: str) -> List[int]:

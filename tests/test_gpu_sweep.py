@@ -59,5 +59,8 @@ def test_learned_proposal_end_to_end():
     for row in res["rows"]:
         assert row["E_plain"] >= e_exact - 1e-9 and row["E_learned"] >= e_exact - 1e-9
         assert 1 <= row["sweeps_learned"] <= cfg.sweeps + 1
-    # the comparison is reported, not gated: both means are finite numbers
-    assert np.isfinite(res["mean_sweeps_plain"]) and np.isfinite(res["mean_sweeps_learned"])
+    # the paired comparison is reported, not gated (the run of one seed is chaotic; a small training
+    # set shows no reliable gain): wins, ties and losses cover the seeds and the sign test is a p-value
+    print({k: res[k] for k in ("wins", "ties", "losses", "sign_test_p", "mean_sweep_difference", "mean_dE_final")})
+    assert res["wins"] + res["ties"] + res["losses"] == len(res["rows"])
+    assert 0.0 < res["sign_test_p"] <= 1.0 and np.isfinite(res["mean_dE_final"])

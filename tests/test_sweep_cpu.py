@@ -51,20 +51,49 @@ def test_plain_sweep_is_variational_monotone_and_follows_the_schedule():
 
 
 def test_a_proposer_that_never_moves_is_never_accepted():
+    """As an extra candidate a zero step never wins, and the random candidates are the plain run's:
+    the learned run reproduces the plain run exactly."""
     h1, eri = sw.hamiltonian(CFG)
     be = OracleBackend(h1, eri, CFG.N, CFG.n_alpha, CFG.n_beta)
     n_k = CFG.N * (CFG.N - 1) // 2
     plain = sw.run_sweep(CFG, seed=2, backend=be)
     res = sw.run_sweep(CFG, seed=2, backend=be, proposer=lambda x: np.zeros((len(x), n_k)))
-    assert res.learned_accepted == 0
-    assert res.proposals == CFG.R * sum(res.M)
-    # zero steps take the place of random ones: never better than the plain run's first sweep
-    assert res.energies[0] >= plain.energies[0] - 1e-9 or res.accepted <= plain.accepted
+    assert res.learned_accepted == 0 and res.learned_births == 0
+    assert res.proposals == (CFG.R + 1) * sum(res.M)
+    assert res.energies == plain.energies and res.accepted == plain.accepted
+    # in the replace mode the zero step takes the place of a random one
+    rcfg = sw.SweepConfig(**{**CFG.__dict__, "learned_mode": "replace"})
+    rep = sw.run_sweep(rcfg, seed=2, backend=be, proposer=lambda x: np.zeros((len(x), n_k)))
+    assert rep.learned_accepted == 0 and rep.proposals == CFG.R * sum(rep.M)
+    assert np.all(np.diff(rep.energies) <= 1e-10)
+
+
+def test_a_good_extra_candidate_is_taken_and_never_hurts_a_step():
+    """A proposer that returns a fixed nonzero step is an extra candidate: with the plain run's random
+    candidates also on offer, the first sweep (one state) ends at an energy no higher than the plain
+    run's, and the energies stay monotone."""
+    h1, eri = sw.hamiltonian(CFG)
+    be = OracleBackend(h1, eri, CFG.N, CFG.n_alpha, CFG.n_beta)
+    n_k = CFG.N * (CFG.N - 1) // 2
+    plain = sw.run_sweep(CFG, seed=3, backend=be)
+    big = lambda x: np.tile(0.3 * np.ones(n_k) / np.sqrt(n_k), (len(x), 1))
+    res = sw.run_sweep(CFG, seed=3, backend=be, proposer=big)
+    assert res.energies[0] <= plain.energies[0] + 1e-10
     assert np.all(np.diff(res.energies) <= 1e-10)
 
 
+def test_paired_summary_sign_test():
+    rows = [{"sweeps_plain": 10, "sweeps_learned": s, "dE_final": d} for s, d in
+            [(8, -1.0), (9, -0.5), (10, 0.0), (12, 0.2), (7, -0.1), (6, -0.3)]]
+    out = sw.paired_summary(rows)
+    assert (out["wins"], out["ties"], out["losses"]) == (4, 1, 1)
+    assert abs(out["sign_test_p"] - 2 * (1 + 5) / 32) < 1e-12       # n = 5, k = 1
+    assert abs(out["mean_sweep_difference"] - (-2 - 1 + 0 + 2 - 3 - 4) / 6) < 1e-12
+    assert out["learned_lower_or_equal_final"] == 5
+
+
 def test_sweeps_to_reach_and_training_rows():
-    r = sw.SweepResult([-1.0, -1.5, -1.5, -2.0], [1, 1, 2, 2], 0, 0, 0, [])
+    r = sw.SweepResult([-1.0, -1.5, -1.5, -2.0], [1, 1, 2, 2], 0, 0, 0, [], 0)
     assert sw.sweeps_to_reach(r, -1.5) == 2 and sw.sweeps_to_reach(r, -2.0) == 4 and sw.sweeps_to_reach(r, -3) == 5
     rec = [(np.ones(3), np.zeros(2), 2.0), (np.zeros(3), np.ones(2), 6.0)]
     X, T, w = sw.training_set(rec)
