@@ -417,6 +417,11 @@ def run_native(args):
                                 "8 n^3 per m x n charge block (LAPACK-SVD-equivalent), counted in the kernel"
                                 if top == "rotate_pairs_kernel" else "algorithmic FLOPs of the blocks computed"),
             "breakdown_ms": {k: v[0] for k, v in kern.items()},
+            "kernels": {k: {"ms_per_step": v[0], "work_per_step": v[1], "bound": v[2], "unit": v[4],
+                            "achieved": ((v[1] / (v[0] / 1e3)) / (1e12 if v[4] == "TFLOP/s" else 1e9)) if v[0] > 0 else 0.0,
+                            "frac": (((v[1] / (v[0] / 1e3)) / (1e12 if v[4] == "TFLOP/s" else 1e9)) / v[3])
+                            if v[0] > 0 and v[3] else None}
+                        for k, v in kern.items()},
             "breakdown_scope": ("kernels of the main stream; in the sliced and charge-block forms the (i, i) "
                                 "pairs, which need no rotation, contract on a second stream beside the "
                                 "rotation kernel and are not in the breakdown")}
