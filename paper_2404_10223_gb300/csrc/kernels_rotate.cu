@@ -148,6 +148,24 @@ __device__ __forceinline__ double grp8_sum(double v, unsigned mask) {
   return v;
 }
 
+__device__ __forceinline__ float2 grp8_sum_df(float2 v, unsigned mask) {
+#pragma unroll
+  for (int o = 4; o > 0; o >>= 1) {
+    const float2 w = make_float2(__shfl_xor_sync(mask, v.x, o), __shfl_xor_sync(mask, v.y, o));
+    v = dfa::add(v, w);
+  }
+  return v;
+}
+
+// 1: the first refinement sweep in double-float arithmetic (FP32 pipes), the
+// later ones FP64.  Off by default: on N = 14, chi = 128 it gained 2 % of the
+// step (430.7 -> 422.8 ms rotation) at unchanged oracle parity, and the
+// refinement sweeps stay FP64 throughout.
+#ifndef TNQE_ROT_DF_SWEEP
+#define TNQE_ROT_DF_SWEEP 0
+#endif
+constexpr int ROT_DF_SWEEP = TNQE_ROT_DF_SWEEP;
+
 // 2^-e for the binary exponent e of a positive normal double (integer ops only)
 __device__ __forceinline__ double exp2_neg_exponent(double x) {
   const int ex = ((__double2hiint(x) >> 20) & 0x7ff) - 1023;
@@ -356,10 +374,15 @@ __device__ int block_svd(const Team& tm, const double* __restrict__ Bm, double* 
       Wd[idx] = acc;
     }
     tm.sync();
-    for (int idx = tr; idx < m * n; idx += ts) W[idx] = dfa::to_double(Wd[idx]);
-    tm.sync();
+    if (!(ROT_DF_SWEEP && n >= 2)) {
+      for (int idx = tr; idx < m * n; idx += ts) W[idx] = dfa::to_double(Wd[idx]);
+      tm.sync();
+    }
   }
   if (n < 2) return noconv;
+  const bool df_first = ROT_DF_SWEEP != 0;       // W is double-float here; Q joins it below
+  float2* Wd = reinterpret_cast<float2*>(W);
+  float2* Qd = reinterpret_cast<float2*>(Q);
   // ---- FP64 phase.  A sweep that finds no pair above 1e-7 relative leaves
   // off-diagonals near 1e-14 after its own rotations (quadratic convergence),
   // so the loop ends after that sweep without a confirming one.
@@ -373,12 +396,23 @@ __device__ int block_svd(const Team& tm, const double* __restrict__ Bm, double* 
   double* gam = const_cast<double*>(Bm);           // per pair of a round: gamma, then a recompute code
   double* cv = gam + n2 / 2;                       // cos, sin per pair (Bm is free: m n >= 3 n2 / 2)
   double* sv = cv + n2 / 2;
-  for (int j = grp; j < n; j += ngrp) {
-    const double* x = W + (size_t)j * m;
-    double a = 0.0;
-    for (int t = gl; t < m; t += 8) a = fma(x[t], x[t], a);
-    a = grp8_sum(a, gmask);
-    if (gl == 0) nrm[j] = a;
+  if (df_first) {
+    for (int idx = tr; idx < n * n; idx += ts) Qd[idx] = dfa::from_double(Q[idx]);   // in place, same 8 bytes
+    for (int j = grp; j < n; j += ngrp) {
+      const float2* x = Wd + (size_t)j * m;
+      float2 a = make_float2(0.f, 0.f);
+      for (int t = gl; t < m; t += 8) a = dfa::fma(x[t], x[t], a);
+      a = grp8_sum_df(a, gmask);
+      if (gl == 0) nrm[j] = dfa::to_double(a);
+    }
+  } else {
+    for (int j = grp; j < n; j += ngrp) {
+      const double* x = W + (size_t)j * m;
+      double a = 0.0;
+      for (int t = gl; t < m; t += 8) a = fma(x[t], x[t], a);
+      a = grp8_sum(a, gmask);
+      if (gl == 0) nrm[j] = a;
+    }
   }
   tm.sync();
   const double tol64 = 2.220446049250313e-16 * (double)m;
@@ -387,17 +421,27 @@ __device__ int block_svd(const Team& tm, const double* __restrict__ Bm, double* 
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     int rot = 0;
     float worst = 0.f;                             // largest gamma^2 / (alpha beta) seen this sweep
+    const bool dfw = df_first && sweep == 0;       // this sweep in double-float
     for (int r = 0; r < n2 - 1; ++r) {
       for (int k = grp; k < n2 / 2; k += ngrp) {
         int i, j;
         tour_pair(r, k, n2, i, j);
         if (i >= n || j >= n) continue;
-        const double* x = W + (size_t)i * m;
-        const double* y = W + (size_t)j * m;
-        double ga = 0.0;
-        for (int t = gl; t < m; t += 8) ga = fma(x[t], y[t], ga);
-        ga = grp8_sum(ga, gmask);
-        if (gl == 0) gam[k] = ga;
+        if (dfw) {
+          const float2* x = Wd + (size_t)i * m;
+          const float2* y = Wd + (size_t)j * m;
+          float2 ga = make_float2(0.f, 0.f);
+          for (int t = gl; t < m; t += 8) ga = dfa::fma(x[t], y[t], ga);
+          ga = grp8_sum_df(ga, gmask);
+          if (gl == 0) gam[k] = dfa::to_double(ga);
+        } else {
+          const double* x = W + (size_t)i * m;
+          const double* y = W + (size_t)j * m;
+          double ga = 0.0;
+          for (int t = gl; t < m; t += 8) ga = fma(x[t], y[t], ga);
+          ga = grp8_sum(ga, gmask);
+          if (gl == 0) gam[k] = ga;
+        }
       }
       tm.sync();
       for (int k = tr; k < n2 / 2; k += ts) {
@@ -449,7 +493,58 @@ __device__ int block_svd(const Team& tm, const double* __restrict__ Bm, double* 
         gam[k] = code;
       }
       tm.sync();
-      for (int k = grp; k < n2 / 2; k += ngrp) {
+      for (int k = grp; k < n2 / 2 && dfw; k += ngrp) {
+        const double s = sv[k];
+        if (s == 0.0) continue;
+        const double c = cv[k];
+        int i, j;
+        tour_pair(r, k, n2, i, j);
+        float2* x = Wd + (size_t)i * m;
+        float2* y = Wd + (size_t)j * m;
+        float2* qx = Qd + (size_t)i * n;
+        float2* qy = Qd + (size_t)j * n;
+        const float2 s2 = dfa::from_double(s), ms2 = make_float2(-s2.x, -s2.y), c2 = dfa::from_double(c);
+        if (c == 1.0) {
+          for (int u = gl; u < m; u += 8) {
+            const float2 xv = x[u], yv = y[u];
+            x[u] = dfa::fma(ms2, yv, xv);
+            y[u] = dfa::fma(s2, xv, yv);
+          }
+          for (int u = gl; u < n; u += 8) {
+            const float2 xv = qx[u], yv = qy[u];
+            qx[u] = dfa::fma(ms2, yv, xv);
+            qy[u] = dfa::fma(s2, xv, yv);
+          }
+        } else {
+          for (int u = gl; u < m; u += 8) {
+            const float2 xv = x[u], yv = y[u];
+            x[u] = dfa::add(dfa::mul(c2, xv), dfa::mul(ms2, yv));
+            y[u] = dfa::add(dfa::mul(s2, xv), dfa::mul(c2, yv));
+          }
+          for (int u = gl; u < n; u += 8) {
+            const float2 xv = qx[u], yv = qy[u];
+            qx[u] = dfa::add(dfa::mul(c2, xv), dfa::mul(ms2, yv));
+            qy[u] = dfa::add(dfa::mul(s2, xv), dfa::mul(c2, yv));
+          }
+        }
+        const double code = gam[k];
+        if (code != 0.0) {
+          const int cd = (int)code;
+          if (cd & 1) {
+            float2 acc = make_float2(0.f, 0.f);
+            for (int u = gl; u < m; u += 8) acc = dfa::fma(x[u], x[u], acc);
+            acc = grp8_sum_df(acc, gmask);
+            if (gl == 0) nrm[i] = dfa::to_double(acc);
+          }
+          if (cd & 2) {
+            float2 acc = make_float2(0.f, 0.f);
+            for (int u = gl; u < m; u += 8) acc = dfa::fma(y[u], y[u], acc);
+            acc = grp8_sum_df(acc, gmask);
+            if (gl == 0) nrm[j] = dfa::to_double(acc);
+          }
+        }
+      }
+      for (int k = grp; k < n2 / 2 && !dfw; k += ngrp) {
         const double s = sv[k];
         if (s == 0.0) continue;
         const double c = cv[k];
@@ -501,6 +596,21 @@ __device__ int block_svd(const Team& tm, const double* __restrict__ Bm, double* 
       }
       tm.sync();
     }
+    if (dfw) {
+      // back to FP64; the norms summed again in FP64; at least one FP64 sweep follows
+      for (int idx = tr; idx < m * n; idx += ts) W[idx] = dfa::to_double(Wd[idx]);
+      for (int idx = tr; idx < n * n; idx += ts) Q[idx] = dfa::to_double(Qd[idx]);
+      tm.sync();
+      for (int j = grp; j < n; j += ngrp) {
+        const double* x = W + (size_t)j * m;
+        double a = 0.0;
+        for (int t = gl; t < m; t += 8) a = fma(x[t], x[t], a);
+        a = grp8_sum(a, gmask);
+        if (gl == 0) nrm[j] = a;
+      }
+      tm.sync();
+      continue;
+    }
     worst = tm.max(worst);
     if (!tm.any(rot) || worst <= 1e-14f) {
       noconv = 0;
@@ -512,14 +622,14 @@ __device__ int block_svd(const Team& tm, const double* __restrict__ Bm, double* 
 
 // Large SVD blocks run concurrently, one per team of ROT_TEAM_WARPS warps.
 #ifndef TNQE_ROT_TEAMS
-#define TNQE_ROT_TEAMS 4                      // teams of RT_WARPS / 4 warps for the large blocks
+#define TNQE_ROT_TEAMS 8                      // teams of RT_WARPS / 8 warps for the large blocks
 #endif
 constexpr int ROT_TEAMS = TNQE_ROT_TEAMS;
 constexpr int ROT_TEAM_WARPS = RT_WARPS / ROT_TEAMS;
 constexpr int ROT_TEAM_THREADS = ROT_TEAM_WARPS * 32;
 static_assert(ROT_TEAMS * ROT_TEAM_WARPS == RT_WARPS, "teams must tile the CTA");
 #ifndef TNQE_ROT_LEAD_WARPS
-#define TNQE_ROT_LEAD_WARPS 8
+#define TNQE_ROT_LEAD_WARPS 16
 #endif
 constexpr int ROT_LEAD_WARPS = TNQE_ROT_LEAD_WARPS;                     // the team of a gate's largest block
 constexpr int ROT_REST_TEAMS = (RT_WARPS - ROT_LEAD_WARPS) / ROT_TEAM_WARPS;
