@@ -82,14 +82,6 @@ struct HostPack {
   }
 };
 
-template <class T> T* dalloc_copy(const std::vector<T>& v, std::vector<void*>& owned) {
-  void* p = nullptr;
-  CK(cudaMalloc(&p, std::max<size_t>(v.size() * sizeof(T), 16)));
-  if (!v.empty()) CK(cudaMemcpy(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
-  owned.push_back(p);
-  return reinterpret_cast<T*>(p);
-}
-
 double binom(int n, int k) {
   if (k < 0 || k > n) return 0.0;
   double r = 1.0;
@@ -223,12 +215,11 @@ BlockTables block_tables(const Mpo& mpo, int N) {
   return T;
 }
 
-struct PairPlan {                        // cached per (i, j): Givens gates on the device
+struct PairPlan {                        // cached per (i, j): Givens gates on the device (in a plan arena)
   int ngates = 0, neg_site = -1;
   double* d_gates = nullptr;
   int* d_site = nullptr;
   int* d_side = nullptr;
-  std::vector<void*> owned;
 };
 
 // A host-to-device copy that a graph replay repeats before launching the graph.
@@ -272,6 +263,7 @@ struct tnqe_ctx {
   bool own_stream = false;
   std::vector<std::unique_ptr<DevMps>> mps;
   std::map<std::pair<int, int>, std::unique_ptr<PairPlan>> plans;
+  std::vector<void*> plan_arenas;        // device memory of the plans, one allocation per batch
   std::string err;
   // rotation workspace
   DBuf rot_work, rot_scratch, rot_meta, rot_small, rot_desc;
@@ -375,37 +367,69 @@ struct RotBatch {
 
 const long long META_INTS = 2 * 32768;
 
-PairPlan* get_plan(tnqe_ctx* c, int i, int j) {
-  auto key = std::make_pair(i, j);
-  auto it = c->plans.find(key);
-  if (it != c->plans.end()) return it->second.get();
+// Givens plans (gates, sites, sides on the device) of every pair (i, j) that has
+// none yet, computed on the host and uploaded together: one allocation and one
+// copy for the whole batch (an arena freed with the states).
+void prepare_plans(tnqe_ctx* c, const std::vector<int>& ii, const std::vector<int>& jj) {
   const int N = c->N;
-  const std::vector<double>& Ui = c->mps[i]->U;
-  const std::vector<double>& Uj = c->mps[j]->U;
-  std::vector<double> V((size_t)N * N);
-  for (int p = 0; p < N; ++p)
-    for (int q = 0; q < N; ++q) {
-      double acc = 0.0;
-      for (int a = 0; a < N; ++a) acc += Ui[(size_t)a * N + p] * Uj[(size_t)a * N + q];
-      V[(size_t)p * N + q] = acc;
+  struct Host {
+    std::pair<int, int> key;
+    int ngates, neg_site;
+    size_t oG, oS, oD;
+  };
+  std::vector<Host> todo;
+  HostPack pk;
+  for (size_t k = 0; k < ii.size(); ++k) {
+    const auto key = std::make_pair(ii[k], jj[k]);
+    if (c->plans.count(key)) continue;
+    bool dup = false;
+    for (const Host& h : todo) dup = dup || h.key == key;
+    if (dup) continue;
+    const std::vector<double>& Ui = c->mps[ii[k]]->U;
+    const std::vector<double>& Uj = c->mps[jj[k]]->U;
+    std::vector<double> V((size_t)N * N);
+    for (int p = 0; p < N; ++p)
+      for (int q = 0; q < N; ++q) {
+        double acc = 0.0;
+        for (int a = 0; a < N; ++a) acc += Ui[(size_t)a * N + p] * Uj[(size_t)a * N + q];
+        V[(size_t)p * N + q] = acc;
+      }
+    GivensPlan gp = givens_plan(V.data(), N);
+    const int ng = (int)gp.gates.size();
+    std::vector<double> G((size_t)std::max(1, ng) * 256, 0.0);
+    std::vector<int> site(std::max(1, ng)), side(std::max(1, ng));
+    for (int g = 0; g < ng; ++g) {
+      gate_matrix(gp.gates[g].c, gp.gates[g].s, &G[(size_t)g * 256]);
+      site[g] = gp.gates[g].site;
+      side[g] = gp.gates[g].side;
     }
-  GivensPlan gp = givens_plan(V.data(), N);
-  auto pp = std::make_unique<PairPlan>();
-  pp->ngates = (int)gp.gates.size();
-  pp->neg_site = gp.neg_site;
-  std::vector<double> G((size_t)std::max(1, pp->ngates) * 256, 0.0);
-  std::vector<int> site(std::max(1, pp->ngates)), side(std::max(1, pp->ngates));
-  for (int g = 0; g < pp->ngates; ++g) {
-    gate_matrix(gp.gates[g].c, gp.gates[g].s, &G[(size_t)g * 256]);
-    site[g] = gp.gates[g].site;
-    side[g] = gp.gates[g].side;
+    Host h{key, ng, gp.neg_site, pk.add(G), pk.add(site), pk.add(side)};
+    todo.push_back(h);
   }
-  pp->d_gates = dalloc_copy(G, pp->owned);
-  pp->d_site = dalloc_copy(site, pp->owned);
-  pp->d_side = dalloc_copy(side, pp->owned);
-  PairPlan* raw = pp.get();
-  c->plans.emplace(key, std::move(pp));
-  return raw;
+  if (todo.empty()) return;
+  void* dev = nullptr;
+  CK(cudaMalloc(&dev, pk.h.size()));
+  c->plan_arenas.push_back(dev);
+  CK(cudaMemcpy(dev, pk.h.data(), pk.h.size(), cudaMemcpyHostToDevice));
+  unsigned char* base = static_cast<unsigned char*>(dev);
+  for (const Host& h : todo) {
+    auto pp = std::make_unique<PairPlan>();
+    pp->ngates = h.ngates;
+    pp->neg_site = h.neg_site;
+    pp->d_gates = reinterpret_cast<double*>(base + h.oG);
+    pp->d_site = reinterpret_cast<int*>(base + h.oS);
+    pp->d_side = reinterpret_cast<int*>(base + h.oD);
+    c->plans.emplace(h.key, std::move(pp));
+  }
+}
+
+PairPlan* get_plan(tnqe_ctx* c, int i, int j) {
+  auto it = c->plans.find(std::make_pair(i, j));
+  if (it == c->plans.end()) {
+    prepare_plans(c, {i}, {j});
+    it = c->plans.find(std::make_pair(i, j));
+  }
+  return it->second.get();
 }
 
 int chi_rot_of(tnqe_ctx* c, int j) { return c->opt.chi_rot > 0 ? c->opt.chi_rot : c->mps[j]->chi; }
@@ -422,6 +446,7 @@ void run_rotations(tnqe_ctx* c, const std::vector<std::pair<int, int>>& pairs, R
     }
   const int np = (int)rb.pair_idx.size();
   if (np == 0) return;
+  prepare_plans(c, rb.ii, rb.jj);
   long long work_total = 0, scratch_total = 0;
   for (int k = 0; k < np; ++k) {
     const DevMps& mj = *c->mps[rb.jj[k]];
@@ -2296,9 +2321,9 @@ tnqe_status tnqe_reset_mps(tnqe_ctx* c) {
     ++c->generation;
     for (auto& m : c->mps) m->free_all();
     c->mps.clear();
-    for (auto& kv : c->plans)
-      for (void* p : kv.second->owned) cudaFree(p);
     c->plans.clear();
+    for (void* p : c->plan_arenas) cudaFree(p);
+    c->plan_arenas.clear();
     c->kept_pair_valid = 0;
     return TNQE_OK;
   } catch (const Error& e) {
@@ -2640,8 +2665,7 @@ void tnqe_destroy(tnqe_ctx* c) {
   cudaSetDevice(c->opt.device);
   if (c->stream) cudaStreamSynchronize(c->stream);
   for (auto& m : c->mps) m->free_all();
-  for (auto& kv : c->plans)
-    for (void* p : kv.second->owned) cudaFree(p);
+  for (void* p : c->plan_arenas) cudaFree(p);
   c->rot_work.release();
   c->rot_scratch.release();
   c->rot_meta.release();
