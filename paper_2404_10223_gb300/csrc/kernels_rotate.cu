@@ -620,24 +620,34 @@ __device__ int block_svd(const Team& tm, const double* __restrict__ Bm, double* 
   return noconv;
 }
 
-// Large SVD blocks run concurrently, one per team of ROT_TEAM_WARPS warps.
+// Large SVD blocks run concurrently on warp teams.  A configuration fixes the
+// CTA size, the number of teams and the lead team (the largest block of each
+// gate).  One 1024-thread CTA per SM: two 512-thread CTAs per SM (all 276
+// rotated pairs of N = 20 at once instead of two waves) took 15.3 s against
+// 8.7 s, since two pairs then share one SM's FP64 units.
 #ifndef TNQE_ROT_TEAMS
 #define TNQE_ROT_TEAMS 8                      // teams of RT_WARPS / 8 warps for the large blocks
 #endif
-constexpr int ROT_TEAMS = TNQE_ROT_TEAMS;
-constexpr int ROT_TEAM_WARPS = RT_WARPS / ROT_TEAMS;
-constexpr int ROT_TEAM_THREADS = ROT_TEAM_WARPS * 32;
-static_assert(ROT_TEAMS * ROT_TEAM_WARPS == RT_WARPS, "teams must tile the CTA");
 #ifndef TNQE_ROT_LEAD_WARPS
 #define TNQE_ROT_LEAD_WARPS 16
 #endif
-constexpr int ROT_LEAD_WARPS = TNQE_ROT_LEAD_WARPS;                     // the team of a gate's largest block
-constexpr int ROT_REST_TEAMS = (RT_WARPS - ROT_LEAD_WARPS) / ROT_TEAM_WARPS;
-constexpr int ROT_SLOTS = 1 + ROT_REST_TEAMS + ROT_LEAD_WARPS / ROT_TEAM_WARPS;
-static_assert(ROT_LEAD_WARPS % ROT_TEAM_WARPS == 0 && ROT_LEAD_WARPS <= RT_WARPS, "lead team splits into teams");
-static_assert(ROT_SLOTS <= 15, "one named barrier per team");
+template <int THREADS, int TEAMS, int LEAD, int MINB>
+struct RotCfg {
+  static constexpr int threads = THREADS, warps = THREADS / 32, min_blocks = MINB;
+  static constexpr int team_warps = warps / TEAMS, team_threads = team_warps * 32, lead = LEAD;
+  static constexpr int rest = (warps - LEAD) / team_warps;         // teams beside the lead team
+  static constexpr int slots = 1 + rest + LEAD / team_warps;       // the lead team splits into teams
+  static_assert(TEAMS * team_warps == warps, "teams must tile the CTA");
+  static_assert(LEAD % team_warps == 0 && LEAD <= warps, "lead team splits into teams");
+  static_assert(slots <= 15, "one named barrier per team");
+};
+using RotWide = RotCfg<RT_THREADS, TNQE_ROT_TEAMS, TNQE_ROT_LEAD_WARPS, 1>;
 
-__global__ void __launch_bounds__(RT_THREADS) rotate_pairs_kernel(const RotDesc* __restrict__ descs) {
+template <class C>
+__global__ void __launch_bounds__(C::threads, C::min_blocks) rotate_pairs_kernel(const RotDesc* __restrict__ descs) {
+  constexpr int RT_THREADS = C::threads, RT_WARPS = C::warps, ROT_TEAM_WARPS = C::team_warps;
+  constexpr int ROT_TEAM_THREADS = C::team_threads, ROT_LEAD_WARPS = C::lead, ROT_REST_TEAMS = C::rest;
+  constexpr int ROT_SLOTS = C::slots;
   const RotDesc& D = descs[blockIdx.x];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int N = D.N;
@@ -1173,14 +1183,14 @@ int launch_rotate(const RotDesc* d_descs, int npairs, int smem_bytes, void* stre
   cudaDeviceGetStreamPriorityRange(&lo, &hi);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)npairs);
-  cfg.blockDim = dim3(RT_THREADS);
+  cfg.blockDim = dim3(RotWide::threads);
   cfg.stream = (cudaStream_t)stream;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributePriority;
   attr[0].val.priority = hi;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  const cudaError_t e = cudaLaunchKernelEx(&cfg, rotate_pairs_kernel, d_descs);
+  const cudaError_t e = cudaLaunchKernelEx(&cfg, rotate_pairs_kernel<RotWide>, d_descs);
   if (e != cudaSuccess) return (int)e;
   return (int)cudaGetLastError();
 }

@@ -377,3 +377,4 @@ def test_reversed_pair_order_matches_oracle():
     with gpu_ctx(w) as g:
         HG, SG = g.matrix_elements(pairs)
     assert np.abs(HG - HB).max() <= TOL_HS and np.abs(SG - SB).max() <= TOL_HS
+
