@@ -13,6 +13,7 @@
 #include <memory>
 #include <stdexcept>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include <cudaTypedefs.h>
@@ -1797,6 +1798,21 @@ void check_ctx(tnqe_ctx* c) {
 // particle-number block structure, (n_alpha, n_beta) sector, left-orthonormal
 // sites 0..N-2), sort every bond by charge and lay the tensors out in that
 // order (host, back to back; offsets in m.off).  Throws Error(TNQE_ERR_ARG).
+// Run f(0..n-1) on up to 8 host threads (static interleaved shares).
+template <class F> void parallel_for(int n, F f) {
+  const int nt = std::max(1, std::min({n, 8, (int)std::thread::hardware_concurrency()}));
+  if (nt <= 1) {
+    for (int i = 0; i < n; ++i) f(i);
+    return;
+  }
+  std::vector<std::thread> th;
+  for (int t = 0; t < nt; ++t)
+    th.emplace_back([&, t]() {
+      for (int i = t; i < n; i += nt) f(i);
+    });
+  for (auto& x : th) x.join();
+}
+
 void order_mps_host(int N, int na, int nb, const double* const* tensors, const int* bond_dims, const double* U,
                     DevMps& m, std::vector<double>& host) {
   if (!tensors || !bond_dims || !U) throw Error(TNQE_ERR_ARG, "null argument");
@@ -1841,8 +1857,10 @@ void order_mps_host(int N, int na, int nb, const double* const* tensors, const i
   }
   if (q[N][0] != na * QSTRIDE + nb) throw Error(TNQE_ERR_ARG, "state is not in the (n_alpha, n_beta) sector");
   // left-orthonormal sites 0..N-2 (columns of different charge have disjoint support)
-  // (the Gram matrix of the columns accumulated row by row, contiguous in memory)
-  for (int s = 0; s + 1 < N; ++s) {
+  // (the Gram matrix of the columns accumulated row by row, contiguous in memory);
+  // the sites are independent and are checked on host threads
+  std::vector<int> bad(N, 0);
+  parallel_for(N - 1, [&](int s) {
     const int cl = bond_dims[s], cr = bond_dims[s + 1];
     const double* A = tensors[s];
     std::vector<double> gram((size_t)cr * cr, 0.0);
@@ -1862,10 +1880,11 @@ void order_mps_host(int N, int na, int nb, const double* const* tensors, const i
     for (int r1 = 0; r1 < cr; ++r1)
       for (int r2 = r1; r2 < cr; ++r2) {
         if (q[s + 1][r1] != q[s + 1][r2]) continue;
-        if (std::fabs(gram[(size_t)r1 * cr + r2] - (r1 == r2 ? 1.0 : 0.0)) > 1e-10)
-          throw Error(TNQE_ERR_ARG, "site " + std::to_string(s) + " is not left-orthonormal");
+        if (std::fabs(gram[(size_t)r1 * cr + r2] - (r1 == r2 ? 1.0 : 0.0)) > 1e-10) bad[s] = 1;
       }
-  }
+  });
+  for (int s = 0; s + 1 < N; ++s)
+    if (bad[s]) throw Error(TNQE_ERR_ARG, "site " + std::to_string(s) + " is not left-orthonormal");
   // sort every bond by charge (a gauge change: the state is unchanged)
   std::vector<std::vector<int>> perm(N + 1);
   m.dims.assign(bond_dims, bond_dims + N + 1);
@@ -1896,10 +1915,16 @@ void order_mps_host(int N, int na, int nb, const double* const* tensors, const i
     for (int s = 0; s < N; ++s) total += (size_t)bond_dims[s] * 4 * bond_dims[s + 1];
     host.resize(total);                          // every entry is written below
   }
-  size_t hoff = 0;
-  for (int s = 0; s < N; ++s) {
+  {
+    size_t hoff = 0;
+    for (int s = 0; s < N; ++s) {
+      m.off[s] = (long long)hoff;
+      hoff += (size_t)bond_dims[s] * 4 * bond_dims[s + 1];
+    }
+  }
+  parallel_for(N, [&](int s) {
     const int cl = bond_dims[s], cr = bond_dims[s + 1];
-    m.off[s] = (long long)hoff;
+    const size_t hoff = (size_t)m.off[s];
     const double* A = tensors[s];
     std::vector<int> qr(cr);
     for (int r = 0; r < cr; ++r) qr[r] = q[s + 1][perm[s + 1][r]];
@@ -1913,8 +1938,7 @@ void order_mps_host(int N, int na, int nb, const double* const* tensors, const i
         for (int r = 0; r < cr; ++r) dst[r] = (qlk == qr[r]) ? src[pr[r]] : 0.0;   // below-tolerance noise outside the blocks
       }
     }
-    hoff += (size_t)cl * 4 * cr;
-  }
+  });
 }
 
 // The Hamiltonian MPO of one state's basis, built on a host thread and packed
