@@ -396,3 +396,23 @@ def test_hermiticity_and_norm_lossless():
     S = Sv.reshape(w.M, w.M)
     assert np.abs(H - H.T).max() <= 1e-12 and np.abs(S - S.T).max() <= 1e-12
     assert np.abs(np.diag(S) - 1.0).max() <= 1e-13
+
+
+def test_pair_list_edge_cases():
+    """An empty pair list, a list of unrotated pairs only, rotated pairs only, and a repeated pair."""
+    w = inputs.workload("n10_chi32")
+    o = oracle_ctx(w)
+    with gpu_ctx(w) as g:
+        H0, S0 = g.matrix_elements([])
+        assert H0.size == 0 and S0.size == 0
+        diag = [(k, k) for k in range(w.M)]
+        Hd, Sd = g.matrix_elements(diag)
+        rot = [(1, 4), (4, 1), (2, 3)]
+        Hr, Sr = g.matrix_elements(rot)
+        Hp, Sp = g.matrix_elements([(2, 3), (2, 3), (0, 0)])
+        with pytest.raises(tnqe.TnqeError):
+            g.matrix_elements([(0, w.M)])
+    HB, SB = o.matrix_elements(diag + rot)
+    assert np.abs(np.concatenate([Hd, Hr]) - HB).max() <= TOL_HS
+    assert np.abs(np.concatenate([Sd, Sr]) - SB).max() <= TOL_HS
+    assert Hp[0] == Hp[1] == Hr[2] and Sp[0] == Sp[1] == Sr[2] and Hp[2] == Hd[0]
