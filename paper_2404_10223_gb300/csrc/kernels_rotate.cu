@@ -159,7 +159,8 @@ __device__ __forceinline__ float2 grp8_sum_df(float2 v, unsigned mask) {
 
 // 1: the first refinement sweep in double-float arithmetic (FP32 pipes), the
 // later ones FP64.  Off by default: on N = 14, chi = 128 it gained 2 % of the
-// step (430.7 -> 422.8 ms rotation) at unchanged oracle parity, and the
+// step (430.7 -> 422.8 ms rotation) at unchanged oracle parity before the FP64
+// sweeps used scaled rotations, and lost 10 % after (382.1 -> 425.5 ms); the
 // refinement sweeps stay FP64 throughout.
 #ifndef TNQE_ROT_DF_SWEEP
 #define TNQE_ROT_DF_SWEEP 0
@@ -214,16 +215,119 @@ struct SubTeam {
   }
 };
 
+// Rotation angle of a column pair from its Gram entries (alpha, beta, gamma):
+// t = tan(theta) = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)), zeta = (beta - alpha) / (2 gamma),
+// the smaller root, so |theta| <= pi / 4.  With ROT_FAST_ANGLE the quotients and
+// the root use the approximate hardware reciprocal and reciprocal square root
+// (a few ulp): an angle is only the start of the next refinement, and every
+// rotation built from it is orthogonal at the working precision.  N = 14,
+// chi = 128: rotation 430.8 -> 421.3 ms per step.
+#ifndef TNQE_ROT_FAST_ANGLE
+#define TNQE_ROT_FAST_ANGLE 1
+#endif
+constexpr int ROT_FAST_ANGLE = TNQE_ROT_FAST_ANGLE;
+__device__ __forceinline__ float jacobi_tan(float al, float be, float ga) {
+  if (ROT_FAST_ANGLE) {
+    const float zeta = __fdividef(be - al, 2.f * ga);
+    const float az = fabsf(zeta);
+    float t;
+    if (az < 1e18f) {
+      const float w = fmaf(zeta, zeta, 1.f);
+      t = __fdividef(1.f, az + w * rsqrtf(w));
+    } else {
+      t = __fdividef(0.5f, az);
+    }
+    return copysignf(t, zeta);
+  }
+  const float zeta = (be - al) / (2.f * ga);
+  return (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + hypotf(1.f, zeta));
+}
+
+// 1: the FP32 sweeps visit the column pairs block by block (blocks of four
+// columns, a block pair per warp), with a team barrier per block round.  N = 14,
+// chi = 128: 430.8 -> 421.4 ms, with the fast angles 411.0 ms.
+#ifndef TNQE_ROT_F32_BLOCKED
+#define TNQE_ROT_F32_BLOCKED 1
+#endif
+constexpr int ROT_F32_BLOCKED = TNQE_ROT_F32_BLOCKED;
+
+// 1: the FP64 sweeps apply scaled rotations.  Column i of W and Q is held as
+// d_i times the stored column; a rotation (c, s = c t) of the true columns
+// becomes x <- x - t (d_j / d_i) y, y <- y + t (d_i / d_j) x on the stored ones
+// (one FMA per element, as for a rotation whose cosine rounds to 1) and
+// d_i <- c d_i, d_j <- c d_j; the scales are multiplied in after the last sweep.
+// The first refinement sweep (angles near 1e-4, cosines below 1) then needs half
+// the FP64 instructions: 413.5 -> 390.5 ms on N = 14, chi = 128.
+#ifndef TNQE_ROT_SCALED
+#define TNQE_ROT_SCALED 1
+#endif
+constexpr int ROT_SCALED = TNQE_ROT_SCALED;
+
+// 1: the FP64 Newton-Schulz step forms E = (I - Q^T Q) / 2 in FP64 and the
+// correction Q E (|E| about 1e-12 after the double-float step) in FP32, then
+// Q <- Q + Q E in FP64; 0: the product Q (1.5 I - 0.5 Q^T Q) in FP64.
+// 390.5 -> 382.1 ms on N = 14, chi = 128.
+#ifndef TNQE_ROT_NS_SPLIT
+#define TNQE_ROT_NS_SPLIT 1
+#endif
+constexpr int ROT_NS_SPLIT = TNQE_ROT_NS_SPLIT;
+
+// One FP32 Jacobi rotation of columns x, y (length m) and of the accumulated
+// rotation columns qx, qy (length n) by an 8-lane group (lane gl of the group,
+// mask gmask).  Skipped when the pair is orthogonal to tol32 relative.
+__device__ __forceinline__ void f32_pair(float* __restrict__ x, float* __restrict__ y, float* __restrict__ qx,
+                                         float* __restrict__ qy, int m, int n, int gl, unsigned gmask, float tol32,
+                                         float& worst, int& rot) {
+  float al = 0.f, be = 0.f, ga = 0.f;
+  for (int t = gl; t < m; t += 8) {
+    const float xv = x[t], yv = y[t];
+    al = fmaf(xv, xv, al);
+    be = fmaf(yv, yv, be);
+    ga = fmaf(xv, yv, ga);
+  }
+  al = grp8_sum(al, gmask);
+  be = grp8_sum(be, gmask);
+  ga = grp8_sum(ga, gmask);
+  float t;
+  if (ROT_FAST_ANGLE) {
+    if (!(al >= 1e-30f) || !(be >= 1e-30f)) return;
+    const float cs = ga * rsqrtf(al) * rsqrtf(be);     // cosine of the angle between x and y
+    if (!(fabsf(cs) > tol32)) return;
+    worst = fmaxf(worst, cs * cs);
+    t = jacobi_tan(al, be, ga);
+  } else {
+    if (ga == 0.f || al < 1e-30f || be < 1e-30f || !(fabsf(ga) > tol32 * sqrtf(al) * sqrtf(be))) return;
+    worst = fmaxf(worst, (ga / al) * (ga / be));
+    t = jacobi_tan(al, be, ga);
+  }
+  const float c = rsqrtf(1.f + t * t), s = c * t;
+  if (s == 0.f) return;
+  for (int u = gl; u < m; u += 8) {
+    const float xv = x[u], yv = y[u];
+    x[u] = c * xv - s * yv;
+    y[u] = s * xv + c * yv;
+  }
+  for (int u = gl; u < n; u += 8) {
+    const float xv = qx[u], yv = qy[u];
+    qx[u] = c * xv - s * yv;
+    qy[u] = s * xv + c * yv;
+  }
+  rot = 1;
+}
+
 // SVD of one block by a team (one warp, or a group of warps), mixed precision.
 // Bm (m x n column-major, n <= m, scaled to max |entry| = 1) is left untouched;
 // on return W = Bm Q with mutually orthogonal columns (FP64) and Q (n x n)
 // orthogonal to FP64 precision.  Steps: FP32 one-sided Jacobi on a copy of Bm
 // until the columns are orthogonal at FP32 level; Q = Newton-Schulz
-// orthogonalisation of the FP32 rotations in FP64; W = Bm Q in FP64; FP64
-// one-sided Jacobi sweeps from that nearly orthogonal start (rotation angles
-// computed in FP32, cos/sin normalised in FP64 so every rotation is orthogonal
-// in FP64).  Column pairs of a tournament round go to the team's 8-lane groups.
-// Returns 1 if a phase hit the sweep limit.
+// orthogonalisation of the FP32 rotations (double-float, then FP64); W = Bm Q
+// in double-float; FP64 one-sided Jacobi sweeps from that nearly orthogonal
+// start (rotation angles computed in FP32, the cosine normalised in FP64 so
+// every rotation is orthogonal in FP64, applied as scaled rotations).  Column
+// pairs go to the team's 8-lane groups: in the FP32 sweeps a warp takes a pair
+// of four-column blocks at a time, in the FP64 sweeps a round of the column
+// tournament is spread over the whole team.  Returns 1 if a phase hit the sweep
+// limit.
 //
 // GB300 executes FP64 at 1/64 of its FP32 rate, so the FP64 sweeps take one
 // dot product per column pair (gamma = x.y): the squared column norms are
@@ -251,44 +355,55 @@ __device__ int block_svd(const Team& tm, const double* __restrict__ Bm, double* 
     for (int sweep = 0; sweep < max_sweeps && !done; ++sweep) {
       int rot = 0;
       float worst = 0.f;                           // largest gamma^2 / (alpha beta) of the sweep
-      for (int r = 0; r < n2 - 1; ++r) {
-        for (int k = grp; k < n2 / 2; k += ngrp) {
-          int i, j;
-          tour_pair(r, k, n2, i, j);
-          if (i >= n || j >= n) continue;
-          float* x = W32 + (size_t)i * m;
-          float* y = W32 + (size_t)j * m;
-          float al = 0.f, be = 0.f, ga = 0.f;
-          for (int t = gl; t < m; t += 8) {
-            const float xv = x[t], yv = y[t];
-            al = fmaf(xv, xv, al);
-            be = fmaf(yv, yv, be);
-            ga = fmaf(xv, yv, ga);
+      if (ROT_F32_BLOCKED) {
+        // Columns in blocks of four.  A sweep first takes the six pairs inside every block
+        // (two blocks per warp), then runs a tournament over the blocks: a warp takes the
+        // block pair (I, J) and its four 8-lane groups run the four matchings
+        // (I_p, J_(p+s) mod 4), s = 0..3.  Every column pair is rotated once per sweep, as
+        // in the column tournament, but the warps of a team meet at a team barrier once per
+        // block round (n / 4 - 1 per sweep instead of n - 1); the rounds inside a block pair
+        // only need warp barriers, since no other warp touches those eight columns.
+        const int wrp = tr >> 5, nwarp = ts >> 5, gw = (tr >> 3) & 3;
+        const int nbk = (n + 3) >> 2, nbk2 = nbk + (nbk & 1);
+        for (int b0 = 2 * wrp; b0 < nbk; b0 += 2 * nwarp) {
+          const int bk = b0 + (gw >> 1), p = gw & 1;
+          for (int rr = 0; rr < 3; ++rr) {
+            const int a = rr == 0 ? 2 * p : p;
+            const int c = rr == 0 ? 2 * p + 1 : (rr == 1 ? p + 2 : 3 - p);
+            const int i = 4 * bk + a, j = 4 * bk + c;
+            if (bk < nbk && j < n)
+              f32_pair(W32 + (size_t)i * m, W32 + (size_t)j * m, Q32 + (size_t)i * n, Q32 + (size_t)j * n, m, n,
+                       gl, gmask, tol32, worst, rot);
+            __syncwarp();
           }
-          al = grp8_sum(al, gmask);
-          be = grp8_sum(be, gmask);
-          ga = grp8_sum(ga, gmask);
-          if (ga == 0.f || al < 1e-30f || be < 1e-30f || !(fabsf(ga) > tol32 * sqrtf(al) * sqrtf(be))) continue;
-          worst = fmaxf(worst, (ga / al) * (ga / be));
-          const float zeta = (be - al) / (2.f * ga);
-          const float t = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + hypotf(1.f, zeta));
-          const float c = rsqrtf(1.f + t * t), s = c * t;
-          if (s == 0.f) continue;
-          for (int u = gl; u < m; u += 8) {
-            const float xv = x[u], yv = y[u];
-            x[u] = c * xv - s * yv;
-            y[u] = s * xv + c * yv;
-          }
-          float* qx = Q32 + (size_t)i * n;
-          float* qy = Q32 + (size_t)j * n;
-          for (int u = gl; u < n; u += 8) {
-            const float xv = qx[u], yv = qy[u];
-            qx[u] = c * xv - s * yv;
-            qy[u] = s * xv + c * yv;
-          }
-          rot = 1;
         }
         tm.sync();
+        for (int r = 0; r < nbk2 - 1; ++r) {
+          for (int k = wrp; k < nbk2 / 2; k += nwarp) {
+            int I, J;
+            tour_pair(r, k, nbk2, I, J);
+            const bool act = I < nbk && J < nbk;
+            for (int s = 0; s < 4; ++s) {
+              const int i = 4 * I + gw, j = 4 * J + ((gw + s) & 3);
+              if (act && i < n && j < n)
+                f32_pair(W32 + (size_t)i * m, W32 + (size_t)j * m, Q32 + (size_t)i * n, Q32 + (size_t)j * n, m, n,
+                         gl, gmask, tol32, worst, rot);
+              __syncwarp();
+            }
+          }
+          tm.sync();
+        }
+      } else {
+        for (int r = 0; r < n2 - 1; ++r) {
+          for (int k = grp; k < n2 / 2; k += ngrp) {
+            int i, j;
+            tour_pair(r, k, n2, i, j);
+            if (i >= n || j >= n) continue;
+            f32_pair(W32 + (size_t)i * m, W32 + (size_t)j * m, Q32 + (size_t)i * n, Q32 + (size_t)j * n, m, n, gl,
+                     gmask, tol32, worst, rot);
+          }
+          tm.sync();
+        }
       }
       // A sweep whose largest relative off-diagonal was below 1e-2 leaves the
       // columns orthogonal to about 1e-4 (quadratic convergence): the FP64
@@ -338,20 +453,38 @@ __device__ int block_svd(const Team& tm, const double* __restrict__ Bm, double* 
       const double* qj = Q + (size_t)j * n;
       double acc = 0.0;
       for (int k = 0; k < n; ++k) acc = fma(qi[k], qj[k], acc);
-      const double v = (i == j ? 1.5 : 0.0) - 0.5 * acc;
-      T[(size_t)j * n + i] = v;
-      T[(size_t)i * n + j] = v;
+      if (ROT_NS_SPLIT) {
+        const float e = (float)(0.5 * ((i == j ? 1.0 : 0.0) - acc));
+        Q32[(size_t)j * n + i] = e;                  // E (the FP32 rotations are no longer needed)
+        Q32[(size_t)i * n + j] = e;
+      } else {
+        const double v = (i == j ? 1.5 : 0.0) - 0.5 * acc;
+        T[(size_t)j * n + i] = v;
+        T[(size_t)i * n + j] = v;
+      }
     }
-    tm.sync();
-    for (int idx = tr; idx < n * n; idx += ts) {
-      const int row = idx % n, col = idx / n;
-      double acc = 0.0;
-      for (int k = 0; k < n; ++k) acc = fma(Q[(size_t)k * n + row], T[(size_t)col * n + k], acc);
-      W[idx] = acc;                                // W used as temporary (m*n >= n*n)
+    if (ROT_NS_SPLIT) {
+      for (int idx = tr; idx < n * n; idx += ts) W32[idx] = (float)Q[idx];   // W32 (m*n >= n*n) is free
+      tm.sync();
+      for (int idx = tr; idx < n * n; idx += ts) {
+        const int row = idx % n, col = idx / n;
+        float acc = 0.f;
+        for (int k = 0; k < n; ++k) acc = fmaf(W32[(size_t)k * n + row], Q32[(size_t)col * n + k], acc);
+        Q[idx] += (double)acc;                       // each thread owns its entry: no read of Q by others below
+      }
+      tm.sync();
+    } else {
+      tm.sync();
+      for (int idx = tr; idx < n * n; idx += ts) {
+        const int row = idx % n, col = idx / n;
+        double acc = 0.0;
+        for (int k = 0; k < n; ++k) acc = fma(Q[(size_t)k * n + row], T[(size_t)col * n + k], acc);
+        W[idx] = acc;                                // W used as temporary (m*n >= n*n)
+      }
+      tm.sync();
+      for (int idx = tr; idx < n * n; idx += ts) Q[idx] = W[idx];
+      tm.sync();
     }
-    tm.sync();
-    for (int idx = tr; idx < n * n; idx += ts) Q[idx] = W[idx];
-    tm.sync();
   }
   // ---- W = Bm Q in double-float: Bm converted in place (the caller no longer needs it),
   // Q copied to double-float in T; W comes back to FP64 in place.  Its error (about
@@ -396,6 +529,7 @@ __device__ int block_svd(const Team& tm, const double* __restrict__ Bm, double* 
   double* gam = const_cast<double*>(Bm);           // per pair of a round: gamma, then a recompute code
   double* cv = gam + n2 / 2;                       // cos, sin per pair (Bm is free: m n >= 3 n2 / 2)
   double* sv = cv + n2 / 2;
+  double* dsc = T + n;                             // column scales of the scaled rotations (n * n >= 2 n)
   if (df_first) {
     for (int idx = tr; idx < n * n; idx += ts) Qd[idx] = dfa::from_double(Q[idx]);   // in place, same 8 bytes
     for (int j = grp; j < n; j += ngrp) {
@@ -403,7 +537,10 @@ __device__ int block_svd(const Team& tm, const double* __restrict__ Bm, double* 
       float2 a = make_float2(0.f, 0.f);
       for (int t = gl; t < m; t += 8) a = dfa::fma(x[t], x[t], a);
       a = grp8_sum_df(a, gmask);
-      if (gl == 0) nrm[j] = dfa::to_double(a);
+      if (gl == 0) {
+        nrm[j] = dfa::to_double(a);
+        dsc[j] = 1.0;
+      }
     }
   } else {
     for (int j = grp; j < n; j += ngrp) {
@@ -411,7 +548,10 @@ __device__ int block_svd(const Team& tm, const double* __restrict__ Bm, double* 
       double a = 0.0;
       for (int t = gl; t < m; t += 8) a = fma(x[t], x[t], a);
       a = grp8_sum(a, gmask);
-      if (gl == 0) nrm[j] = a;
+      if (gl == 0) {
+        nrm[j] = a;
+        dsc[j] = 1.0;
+      }
     }
   }
   tm.sync();
@@ -448,16 +588,18 @@ __device__ int block_svd(const Team& tm, const double* __restrict__ Bm, double* 
         int i, j;
         tour_pair(r, k, n2, i, j);
         double c = 1.0, s = 0.0, code = 0.0;
+        double a1 = 1.0, a2 = 0.0;                   // what the groups apply: (c, s), or the scaled (-t dj/di, t di/dj)
         if (i < n && j < n) {
-          const double al = nrm[i], be = nrm[j], ga = gam[k];
+          const bool scaled = ROT_SCALED && !dfw;
+          const double al = nrm[i], be = nrm[j];
+          const double ga = scaled ? gam[k] * (dsc[i] * dsc[j]) : gam[k];
           // columns below 1e-125 of the block's largest entry are zero at this precision
           if (ga != 0.0 && al >= 1e-250 && be >= 1e-250) {
             const double sc = exp2_neg_exponent(fmax(al, be));
             const float af = (float)(al * sc), bf = (float)(be * sc), gf = (float)(ga * sc);
             if (gf * gf > tol64sq * af * bf) {
               worst = fmaxf(worst, (gf * gf) / (af * bf));
-              const float zeta = (bf - af) / (2.f * gf);
-              const float t32 = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + hypotf(1.f, zeta));
+              const float t32 = jacobi_tan(af, bf, gf);
               const double t = (double)t32;
               if (fabsf(t32) < 7.0e-9f) {            // 1 + t^2 rounds to 1: the rotation is I + t J
                 s = t;
@@ -484,12 +626,24 @@ __device__ int block_svd(const Team& tm, const double* __restrict__ Bm, double* 
                 nrm[i] = na;
                 nrm[j] = nb2;
                 code = (ri ? 1.0 : 0.0) + (rj ? 2.0 : 0.0);
+                if (scaled) {
+                  const double di = dsc[i], dj = dsc[j], rji = dj / di;
+                  a1 = -t * rji;
+                  a2 = t / rji;
+                  if (c != 1.0) {
+                    dsc[i] = c * di;
+                    dsc[j] = c * dj;
+                  }
+                } else {
+                  a1 = c;
+                  a2 = s;
+                }
               }
             }
           }
         }
-        cv[k] = c;
-        sv[k] = s;
+        cv[k] = a1;
+        sv[k] = a2;
         gam[k] = code;
       }
       tm.sync();
@@ -554,7 +708,18 @@ __device__ int block_svd(const Team& tm, const double* __restrict__ Bm, double* 
         double* y = W + (size_t)j * m;
         double* qx = Q + (size_t)i * n;
         double* qy = Q + (size_t)j * n;
-        if (c == 1.0) {
+        if (ROT_SCALED) {                          // c holds -t dj/di, s holds t di/dj
+          for (int u = gl; u < m; u += 8) {
+            const double xv = x[u], yv = y[u];
+            x[u] = fma(c, yv, xv);
+            y[u] = fma(s, xv, yv);
+          }
+          for (int u = gl; u < n; u += 8) {
+            const double xv = qx[u], yv = qy[u];
+            qx[u] = fma(c, yv, xv);
+            qy[u] = fma(s, xv, yv);
+          }
+        } else if (c == 1.0) {
           for (int u = gl; u < m; u += 8) {
             const double xv = x[u], yv = y[u];
             x[u] = fma(-s, yv, xv);
@@ -584,13 +749,13 @@ __device__ int block_svd(const Team& tm, const double* __restrict__ Bm, double* 
             double acc = 0.0;
             for (int u = gl; u < m; u += 8) acc = fma(x[u], x[u], acc);
             acc = grp8_sum(acc, gmask);
-            if (gl == 0) nrm[i] = acc;
+            if (gl == 0) nrm[i] = ROT_SCALED ? acc * (dsc[i] * dsc[i]) : acc;
           }
           if (cd & 2) {
             double acc = 0.0;
             for (int u = gl; u < m; u += 8) acc = fma(y[u], y[u], acc);
             acc = grp8_sum(acc, gmask);
-            if (gl == 0) nrm[j] = acc;
+            if (gl == 0) nrm[j] = ROT_SCALED ? acc * (dsc[j] * dsc[j]) : acc;
           }
         }
       }
@@ -616,6 +781,11 @@ __device__ int block_svd(const Team& tm, const double* __restrict__ Bm, double* 
       noconv = 0;
       break;
     }
+  }
+  if (ROT_SCALED) {                                // true columns: the stored ones times their scales
+    for (int idx = tr; idx < m * n; idx += ts) W[idx] *= dsc[idx / m];
+    for (int idx = tr; idx < n * n; idx += ts) Q[idx] *= dsc[idx / n];
+    tm.sync();
   }
   return noconv;
 }
@@ -1010,23 +1180,39 @@ __global__ void __launch_bounds__(C::threads, C::min_blocks) rotate_pairs_kernel
     __syncthreads();
     // ---- global truncation: k = min(chi_rot, #{sigma > cutoff sigma_1}), at least 1
     const int nsig = s_nsig;
-    if (tid == 0) {
+    if (warp == 0) {
       double smax = 0.0;
-      for (int x = 0; x < nsig; ++x) smax = fmax(smax, sig[x]);
+      for (int x = lane; x < nsig; x += 32) smax = fmax(smax, sig[x]);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) smax = fmax(smax, __shfl_xor_sync(0xffffffffu, smax, o));
+      const double thr = D.cutoff * smax;
       int above = 0;
-      for (int x = 0; x < nsig; ++x) above += (sig[x] > D.cutoff * smax) ? 1 : 0;
-      int keep = above < D.chi_rot ? above : D.chi_rot;
-      if (keep > D.work_cap[a + 1]) keep = D.work_cap[a + 1];
-      if (keep < 1) keep = 1;
-      if (keep > nsig) keep = nsig;
-      s_keep = keep;
+      for (int x = lane; x < nsig; x += 32) above += (sig[x] > thr) ? 1 : 0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) above += __shfl_xor_sync(0xffffffffu, above, o);
+      if (lane == 0) {
+        int keep = above < D.chi_rot ? above : D.chi_rot;
+        if (keep > D.work_cap[a + 1]) keep = D.work_cap[a + 1];
+        if (keep < 1) keep = 1;
+        if (keep > nsig) keep = nsig;
+        s_keep = keep;
+      }
     }
     __syncthreads();
-    for (int x = tid; x < nsig; x += RT_THREADS) {
-      const double v = sig[x];
-      int rank = 0;
-      for (int y = 0; y < nsig; ++y) rank += (sig[y] > v || (sig[y] == v && y < x)) ? 1 : 0;
-      sig_keep[x] = rank < s_keep ? 1 : 0;
+    {
+      // rank of each singular value (ties by index).  The values are non-negative
+      // (+0 or more), and for those the IEEE encodings, read as signed 64-bit
+      // integers, are in numeric order: the comparisons run on the integer units.
+      const long long* sk = reinterpret_cast<const long long*>(sig);
+      for (int x = tid; x < nsig; x += RT_THREADS) {
+        const long long v = sk[x];
+        int rank = 0;
+        for (int y = 0; y < nsig; ++y) {
+          const long long u = sk[y];
+          rank += (u > v || (u == v && y < x)) ? 1 : 0;
+        }
+        sig_keep[x] = rank < s_keep ? 1 : 0;
+      }
     }
     __syncthreads();
     if (tid == 0) {
