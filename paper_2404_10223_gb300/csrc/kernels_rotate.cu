@@ -130,10 +130,13 @@ constexpr int MAXBLK = 1024;
 #ifndef TNQE_ROT_F32_STOP                    // FP32 sweeps end once gamma^2 / (alpha beta) stays below this
 #define TNQE_ROT_F32_STOP 1e-4f
 #endif
+// Blocks with min(rows, cols) >= this go to warp teams, the others one per warp.
+// N = 14, chi = 128 with block-ordered FP32 sweeps and scaled FP64 rotations:
+// 16 -> 367.9 ms rotation, 24 -> 372.9, 32 -> 405.4.
 #ifndef TNQE_ROT_BIG_BLOCK_N
-#define TNQE_ROT_BIG_BLOCK_N 24
+#define TNQE_ROT_BIG_BLOCK_N 16
 #endif
-constexpr int BIG_BLOCK_N = TNQE_ROT_BIG_BLOCK_N;   // blocks with min(rows, cols) >= this go to warp teams
+constexpr int BIG_BLOCK_N = TNQE_ROT_BIG_BLOCK_N;
 
 __device__ __forceinline__ float grp8_sum(float v, unsigned mask) {
   v += __shfl_xor_sync(mask, v, 4);
