@@ -318,6 +318,52 @@ __device__ __forceinline__ void f32_pair(float* __restrict__ x, float* __restric
   rot = 1;
 }
 
+// > 0: in a block pair of the FP32 sweeps, a group keeps its own column
+// (m <= 8 x this) in registers for the pair's four rounds; 10 covers the
+// largest blocks of chi = 128 (12 spills registers and was slower).
+#ifndef TNQE_ROT_F32_REGCOL
+#define TNQE_ROT_F32_REGCOL 10
+#endif
+constexpr int ROT_F32_REGCOL = TNQE_ROT_F32_REGCOL;
+template <int RC>
+__device__ __forceinline__ void f32_pair_reg(float (&xr)[RC], float* __restrict__ y, float* __restrict__ qx,
+                                             float* __restrict__ qy, int m, int n, int gl, unsigned gmask,
+                                             float tol32, float& worst, int& rot) {
+  float yr[RC];
+  float al = 0.f, be = 0.f, ga = 0.f;
+#pragma unroll
+  for (int e = 0; e < RC; ++e) {
+    const int t = gl + 8 * e;
+    yr[e] = t < m ? y[t] : 0.f;
+    al = fmaf(xr[e], xr[e], al);
+    be = fmaf(yr[e], yr[e], be);
+    ga = fmaf(xr[e], yr[e], ga);
+  }
+  al = grp8_sum(al, gmask);
+  be = grp8_sum(be, gmask);
+  ga = grp8_sum(ga, gmask);
+  if (!(al >= 1e-30f) || !(be >= 1e-30f)) return;
+  const float cs = ga * rsqrtf(al) * rsqrtf(be);
+  if (!(fabsf(cs) > tol32)) return;
+  worst = fmaxf(worst, cs * cs);
+  const float t = jacobi_tan(al, be, ga);
+  const float c = rsqrtf(1.f + t * t), s = c * t;
+  if (s == 0.f) return;
+#pragma unroll
+  for (int e = 0; e < RC; ++e) {
+    const float xv = xr[e], yv = yr[e];
+    xr[e] = c * xv - s * yv;
+    const int u = gl + 8 * e;
+    if (u < m) y[u] = s * xv + c * yv;
+  }
+  for (int u = gl; u < n; u += 8) {
+    const float xv = qx[u], yv = qy[u];
+    qx[u] = c * xv - s * yv;
+    qy[u] = s * xv + c * yv;
+  }
+  rot = 1;
+}
+
 // SVD of one block by a team (one warp, or a group of warps), mixed precision.
 // Bm (m x n column-major, n <= m, scaled to max |entry| = 1) is left untouched;
 // on return W = Bm Q with mutually orthogonal columns (FP64) and Q (n x n)
@@ -386,12 +432,39 @@ __device__ int block_svd(const Team& tm, const double* __restrict__ Bm, double* 
             int I, J;
             tour_pair(r, k, nbk2, I, J);
             const bool act = I < nbk && J < nbk;
-            for (int s = 0; s < 4; ++s) {
-              const int i = 4 * I + gw, j = 4 * J + ((gw + s) & 3);
-              if (act && i < n && j < n)
-                f32_pair(W32 + (size_t)i * m, W32 + (size_t)j * m, Q32 + (size_t)i * n, Q32 + (size_t)j * n, m, n,
-                         gl, gmask, tol32, worst, rot);
-              __syncwarp();
+            if (ROT_F32_REGCOL > 0 && m <= 8 * ROT_F32_REGCOL) {
+              constexpr int RC = ROT_F32_REGCOL > 0 ? ROT_F32_REGCOL : 1;
+              const int i = 4 * I + gw;
+              const bool own = act && i < n;
+              float* x = W32 + (size_t)i * m;
+              float xr[RC];
+#pragma unroll
+              for (int e = 0; e < RC; ++e) {
+                const int t = gl + 8 * e;
+                xr[e] = (own && t < m) ? x[t] : 0.f;
+              }
+              for (int s = 0; s < 4; ++s) {
+                const int j = 4 * J + ((gw + s) & 3);
+                if (own && j < n)
+                  f32_pair_reg<RC>(xr, W32 + (size_t)j * m, Q32 + (size_t)i * n, Q32 + (size_t)j * n, m, n, gl, gmask,
+                                   tol32, worst, rot);
+                __syncwarp();
+              }
+              if (own) {
+#pragma unroll
+                for (int e = 0; e < RC; ++e) {
+                  const int t = gl + 8 * e;
+                  if (t < m) x[t] = xr[e];
+                }
+              }
+            } else {
+              for (int s = 0; s < 4; ++s) {
+                const int i = 4 * I + gw, j = 4 * J + ((gw + s) & 3);
+                if (act && i < n && j < n)
+                  f32_pair(W32 + (size_t)i * m, W32 + (size_t)j * m, Q32 + (size_t)i * n, Q32 + (size_t)j * n, m, n,
+                           gl, gmask, tol32, worst, rot);
+                __syncwarp();
+              }
             }
           }
           tm.sync();
@@ -533,6 +606,7 @@ __device__ int block_svd(const Team& tm, const double* __restrict__ Bm, double* 
   double* cv = gam + n2 / 2;                       // cos, sin per pair (Bm is free: m n >= 3 n2 / 2)
   double* sv = cv + n2 / 2;
   double* dsc = T + n;                             // column scales of the scaled rotations (n * n >= 2 n)
+  double* dinv = T + 2 * n;                        // their reciprocals, kept where n * n >= 3 n
   if (df_first) {
     for (int idx = tr; idx < n * n; idx += ts) Qd[idx] = dfa::from_double(Q[idx]);   // in place, same 8 bytes
     for (int j = grp; j < n; j += ngrp) {
@@ -543,6 +617,7 @@ __device__ int block_svd(const Team& tm, const double* __restrict__ Bm, double* 
       if (gl == 0) {
         nrm[j] = dfa::to_double(a);
         dsc[j] = 1.0;
+        if (n >= 3) dinv[j] = 1.0;
       }
     }
   } else {
@@ -554,6 +629,7 @@ __device__ int block_svd(const Team& tm, const double* __restrict__ Bm, double* 
       if (gl == 0) {
         nrm[j] = a;
         dsc[j] = 1.0;
+        if (n >= 3) dinv[j] = 1.0;
       }
     }
   }
@@ -573,9 +649,14 @@ __device__ int block_svd(const Team& tm, const double* __restrict__ Bm, double* 
         if (dfw) {
           const float2* x = Wd + (size_t)i * m;
           const float2* y = Wd + (size_t)j * m;
-          float2 ga = make_float2(0.f, 0.f);
-          for (int t = gl; t < m; t += 8) ga = dfa::fma(x[t], y[t], ga);
-          ga = grp8_sum_df(ga, gmask);
+          float2 ga = make_float2(0.f, 0.f), gb = make_float2(0.f, 0.f);   // two chains
+          int t = gl;
+          for (; t + 8 < m; t += 16) {
+            ga = dfa::fma(x[t], y[t], ga);
+            gb = dfa::fma(x[t + 8], y[t + 8], gb);
+          }
+          if (t < m) ga = dfa::fma(x[t], y[t], ga);
+          ga = grp8_sum_df(dfa::add(ga, gb), gmask);
           if (gl == 0) gam[k] = dfa::to_double(ga);
         } else {
           const double* x = W + (size_t)i * m;
@@ -593,7 +674,7 @@ __device__ int block_svd(const Team& tm, const double* __restrict__ Bm, double* 
         double c = 1.0, s = 0.0, code = 0.0;
         double a1 = 1.0, a2 = 0.0;                   // what the groups apply: (c, s), or the scaled (-t dj/di, t di/dj)
         if (i < n && j < n) {
-          const bool scaled = ROT_SCALED && !dfw;
+          const bool scaled = ROT_SCALED != 0;
           const double al = nrm[i], be = nrm[j];
           const double ga = scaled ? gam[k] * (dsc[i] * dsc[j]) : gam[k];
           // columns below 1e-125 of the block's largest entry are zero at this precision
@@ -604,10 +685,11 @@ __device__ int block_svd(const Team& tm, const double* __restrict__ Bm, double* 
               worst = fmaxf(worst, (gf * gf) / (af * bf));
               const float t32 = jacobi_tan(af, bf, gf);
               const double t = (double)t32;
+              double w = 1.0;
               if (fabsf(t32) < 7.0e-9f) {            // 1 + t^2 rounds to 1: the rotation is I + t J
                 s = t;
               } else {
-                const double w = fma(t, t, 1.0);
+                w = fma(t, t, 1.0);
                 c = (double)rsqrtf((float)w);
                 c = c * fma(-0.5 * w, c * c, 1.5);
                 c = c * fma(-0.5 * w, c * c, 1.5);
@@ -630,12 +712,20 @@ __device__ int block_svd(const Team& tm, const double* __restrict__ Bm, double* 
                 nrm[j] = nb2;
                 code = (ri ? 1.0 : 0.0) + (rj ? 2.0 : 0.0);
                 if (scaled) {
-                  const double di = dsc[i], dj = dsc[j], rji = dj / di;
+                  // d_j / d_i and d_i / d_j from the kept reciprocals (1 / c = w c)
+                  const double di = dsc[i], dj = dsc[j];
+                  const bool inv = n >= 3;
+                  const double rji = inv ? dj * dinv[i] : dj / di, rij = inv ? di * dinv[j] : di / dj;
                   a1 = -t * rji;
-                  a2 = t / rji;
+                  a2 = t * rij;
                   if (c != 1.0) {
                     dsc[i] = c * di;
                     dsc[j] = c * dj;
+                    if (inv) {
+                      const double ic = w * c;
+                      dinv[i] *= ic;
+                      dinv[j] *= ic;
+                    }
                   }
                 } else {
                   a1 = c;
@@ -661,7 +751,18 @@ __device__ int block_svd(const Team& tm, const double* __restrict__ Bm, double* 
         float2* qx = Qd + (size_t)i * n;
         float2* qy = Qd + (size_t)j * n;
         const float2 s2 = dfa::from_double(s), ms2 = make_float2(-s2.x, -s2.y), c2 = dfa::from_double(c);
-        if (c == 1.0) {
+        if (ROT_SCALED) {                          // c2 holds -t dj/di, s2 holds t di/dj
+          for (int u = gl; u < m; u += 8) {
+            const float2 xv = x[u], yv = y[u];
+            x[u] = dfa::fma(c2, yv, xv);
+            y[u] = dfa::fma(s2, xv, yv);
+          }
+          for (int u = gl; u < n; u += 8) {
+            const float2 xv = qx[u], yv = qy[u];
+            qx[u] = dfa::fma(c2, yv, xv);
+            qy[u] = dfa::fma(s2, xv, yv);
+          }
+        } else if (c == 1.0) {
           for (int u = gl; u < m; u += 8) {
             const float2 xv = x[u], yv = y[u];
             x[u] = dfa::fma(ms2, yv, xv);
@@ -691,13 +792,13 @@ __device__ int block_svd(const Team& tm, const double* __restrict__ Bm, double* 
             float2 acc = make_float2(0.f, 0.f);
             for (int u = gl; u < m; u += 8) acc = dfa::fma(x[u], x[u], acc);
             acc = grp8_sum_df(acc, gmask);
-            if (gl == 0) nrm[i] = dfa::to_double(acc);
+            if (gl == 0) nrm[i] = ROT_SCALED ? dfa::to_double(acc) * (dsc[i] * dsc[i]) : dfa::to_double(acc);
           }
           if (cd & 2) {
             float2 acc = make_float2(0.f, 0.f);
             for (int u = gl; u < m; u += 8) acc = dfa::fma(y[u], y[u], acc);
             acc = grp8_sum_df(acc, gmask);
-            if (gl == 0) nrm[j] = dfa::to_double(acc);
+            if (gl == 0) nrm[j] = ROT_SCALED ? dfa::to_double(acc) * (dsc[j] * dsc[j]) : dfa::to_double(acc);
           }
         }
       }
@@ -774,7 +875,7 @@ __device__ int block_svd(const Team& tm, const double* __restrict__ Bm, double* 
         double a = 0.0;
         for (int t = gl; t < m; t += 8) a = fma(x[t], x[t], a);
         a = grp8_sum(a, gmask);
-        if (gl == 0) nrm[j] = a;
+        if (gl == 0) nrm[j] = ROT_SCALED ? a * (dsc[j] * dsc[j]) : a;
       }
       tm.sync();
       continue;
@@ -801,8 +902,11 @@ __device__ int block_svd(const Team& tm, const double* __restrict__ Bm, double* 
 #ifndef TNQE_ROT_TEAMS
 #define TNQE_ROT_TEAMS 8                      // teams of RT_WARPS / 8 warps for the large blocks
 #endif
+// The lead team: 12 warps (five teams of four beside it) measured 360.0 ms
+// against 365.1 ms for 16 warps on N = 14, chi = 128, together with the
+// register-held columns of the FP32 block pairs.
 #ifndef TNQE_ROT_LEAD_WARPS
-#define TNQE_ROT_LEAD_WARPS 16
+#define TNQE_ROT_LEAD_WARPS 12
 #endif
 template <int THREADS, int TEAMS, int LEAD, int MINB>
 struct RotCfg {
