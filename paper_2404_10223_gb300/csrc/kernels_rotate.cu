@@ -125,7 +125,6 @@ __device__ int jacobi_block(double* W, double* Q, int m, int n, int max_sweeps, 
 #define TNQE_ROT_THREADS 1024
 #endif
 constexpr int RT_THREADS = TNQE_ROT_THREADS;
-constexpr int RT_WARPS = RT_THREADS / 32;
 constexpr int MAXBLK = 1024;
 #ifndef TNQE_ROT_F32_STOP                    // FP32 sweeps end once gamma^2 / (alpha beta) stays below this
 #define TNQE_ROT_F32_STOP 1e-4f
@@ -900,7 +899,7 @@ __device__ int block_svd(const Team& tm, const double* __restrict__ Bm, double* 
 // rotated pairs of N = 20 at once instead of two waves) took 15.3 s against
 // 8.7 s, since two pairs then share one SM's FP64 units.
 #ifndef TNQE_ROT_TEAMS
-#define TNQE_ROT_TEAMS 8                      // teams of RT_WARPS / 8 warps for the large blocks
+#define TNQE_ROT_TEAMS 8                      // teams of (CTA warps) / 8 warps for the large blocks
 #endif
 // The lead team: 12 warps (five teams of four beside it) measured 360.0 ms
 // against 365.1 ms for 16 warps on N = 14, chi = 128, together with the
@@ -931,12 +930,11 @@ __global__ void __launch_bounds__(C::threads, C::min_blocks) rotate_pairs_kernel
 
   __shared__ int lutL[QSPACE], lutM[QSPACE], lutR[QSPACE];
   __shared__ SectorTable secL, secM, secR;
-  __shared__ double G[256];
   __shared__ int gnz_n[16], gnz_k[16][16];
   __shared__ double gnz_v[16][16];
   __shared__ double sig[MAXSIG];
   __shared__ unsigned char sig_keep[MAXSIG];
-  __shared__ short s_ord[MAXBLK];
+  __shared__ short s_ord[QSPACE];                 // blocks of a gate: one per charge of the new bond
   __shared__ int s_nblk, s_nnew, s_total, s_nsig, s_keep, s_status, s_nbig;
   __shared__ float s_tscr[ROT_SLOTS];
   __shared__ int s_tbi[ROT_SLOTS], s_next_big, s_next_small;
@@ -985,7 +983,6 @@ __global__ void __launch_bounds__(C::threads, C::min_blocks) rotate_pairs_kernel
         if (x < W4) dL[x] = v; else if (x < 2 * W4) dM[x - W4] = v; else dR[x - 2 * W4] = v;
       }
     }
-    for (int x = tid; x < 256; x += RT_THREADS) G[x] = D.gates[(size_t)g * 256 + x];
     __syncthreads();
     for (int x = tid; x < secL.nsec; x += RT_THREADS) lutL[secL.q[x]] = x;
     for (int x = tid; x < secM.nsec; x += RT_THREADS) lutM[secM.q[x]] = x;
@@ -993,7 +990,7 @@ __global__ void __launch_bounds__(C::threads, C::min_blocks) rotate_pairs_kernel
     if (tid < 16) {                       // nonzero inputs of each gate row
       int c = 0;
       for (int K = 0; K < 16; ++K) {
-        const double v = G[tid * 16 + K];
+        const double v = D.gates[(size_t)g * 256 + tid * 16 + K];
         if (v != 0.0) {
           gnz_k[tid][c] = K;
           gnz_v[tid][c] = v;
@@ -1106,8 +1103,8 @@ __global__ void __launch_bounds__(C::threads, C::min_blocks) rotate_pairs_kernel
       const long long cb = (long long)(B.nr > B.nc ? B.nr : B.nc) * (B.nr < B.nc ? B.nr : B.nc) * (B.nr < B.nc ? B.nr : B.nc);
       int rank = 0;
       for (int b2 = 0; b2 < nnew; ++b2) {
-        const NewBlk& C = nb[b2];
-        const long long cc = (long long)(C.nr > C.nc ? C.nr : C.nc) * (C.nr < C.nc ? C.nr : C.nc) * (C.nr < C.nc ? C.nr : C.nc);
+        const NewBlk& B2 = nb[b2];
+        const long long cc = (long long)(B2.nr > B2.nc ? B2.nr : B2.nc) * (B2.nr < B2.nc ? B2.nr : B2.nc) * (B2.nr < B2.nc ? B2.nr : B2.nc);
         rank += (cc > cb || (cc == cb && b2 < b)) ? 1 : 0;
       }
       s_ord[rank] = (short)b;
