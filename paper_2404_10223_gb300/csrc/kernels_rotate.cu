@@ -935,6 +935,7 @@ __global__ void __launch_bounds__(C::threads, C::min_blocks) rotate_pairs_kernel
   __shared__ double sig[MAXSIG];
   __shared__ unsigned char sig_keep[MAXSIG];
   __shared__ short s_ord[QSPACE];                 // blocks of a gate: one per charge of the new bond
+  __shared__ long long s_scan[QSPACE / 32][4];
   __shared__ int s_nblk, s_nnew, s_total, s_nsig, s_keep, s_status, s_nbig;
   __shared__ float s_tscr[ROT_SLOTS];
   __shared__ int s_tbi[ROT_SLOTS], s_next_big, s_next_small;
@@ -1050,12 +1051,15 @@ __global__ void __launch_bounds__(C::threads, C::min_blocks) rotate_pairs_kernel
         D.theta[(((size_t)l * 4 + B.k1) * 4 + B.k2) * chr + r] = acc;
       }
     }
-    // ---- blocks of the new middle bond, ascending charge
-    if (tid == 0) {
-      int nnew = 0, nsig = 0;
-      long long wofs = 0, qofs = 0;
-      for (int q = 0; q < QSPACE; ++q) {
-        NewBlk B;
+    // ---- blocks of the new middle bond, ascending charge: one thread per charge q
+    // of the new bond, offsets from prefix sums over q
+    {
+      static_assert(QSPACE % 32 == 0 && QSPACE <= C::threads, "one thread per charge");
+      NewBlk B;
+      int mm = 0, nn = 0;
+      bool ex = false;
+      if (tid < QSPACE) {
+        const int q = tid;
         B.q = q;
         int nr = 0, nc = 0;
         for (int k = 0; k < 4; ++k) {
@@ -1070,30 +1074,65 @@ __global__ void __launch_bounds__(C::threads, C::min_blocks) rotate_pairs_kernel
           B.coloff[k] = nc;
           if (sR >= 0) nc += secR.dim[sR];
         }
-        if (nr == 0 || nc == 0) continue;
         B.nr = nr;
         B.nc = nc;
-        const int mm = nr > nc ? nr : nc, nn = nr > nc ? nc : nr;
-        B.wofs = wofs;
-        B.qofs = qofs;
-        B.sofs = nsig;
-        B.kept = 0;
-        B.newoff = 0;
-        B.scale = 1.0;
-        wofs += (long long)mm * nn;
-        qofs += (long long)nn * nn;
-        s_flops += 4.0 * mm * nn * nn + 8.0 * nn * nn * nn + 8.0 * mm * nn;
-        nsig += nn;
-        if (nnew < nb_cap && nsig <= MAXSIG) nb[nnew] = B;
-        ++nnew;
+        ex = nr > 0 && nc > 0;
+        if (ex) {
+          mm = nr > nc ? nr : nc;
+          nn = nr > nc ? nc : nr;
+        }
       }
-      if (nnew > nb_cap || nsig > MAXSIG) {
-        s_status |= STATUS_OVERFLOW;
-        nnew = 0;
-        nsig = 0;
+      // inclusive scans of (block, m n, n n, n) over the charges, warp by warp
+      long long v0 = ex ? 1 : 0, v1 = (long long)mm * nn, v2 = (long long)nn * nn, v3 = nn;
+      if (tid < QSPACE) {
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const long long t0 = __shfl_up_sync(0xffffffffu, v0, o), t1 = __shfl_up_sync(0xffffffffu, v1, o);
+          const long long t2 = __shfl_up_sync(0xffffffffu, v2, o), t3 = __shfl_up_sync(0xffffffffu, v3, o);
+          if (lane >= o) {
+            v0 += t0;
+            v1 += t1;
+            v2 += t2;
+            v3 += t3;
+          }
+        }
+        if (lane == 31) {
+          s_scan[warp][0] = v0;
+          s_scan[warp][1] = v1;
+          s_scan[warp][2] = v2;
+          s_scan[warp][3] = v3;
+        }
       }
-      s_nnew = nnew;
-      s_nsig = nsig;
+      __syncthreads();
+      if (tid < QSPACE) {
+        for (int w = 0; w < warp; ++w) {
+          v0 += s_scan[w][0];
+          v1 += s_scan[w][1];
+          v2 += s_scan[w][2];
+          v3 += s_scan[w][3];
+        }
+        if (ex) {                                  // exclusive offsets: inclusive minus own
+          const int idx = (int)(v0 - 1);
+          B.wofs = v1 - (long long)mm * nn;
+          B.qofs = v2 - (long long)nn * nn;
+          B.sofs = (int)(v3 - nn);
+          B.kept = 0;
+          B.newoff = 0;
+          B.scale = 1.0;
+          if (idx < nb_cap && v3 <= MAXSIG) nb[idx] = B;
+          atomicAdd(&s_flops, 4.0 * mm * nn * nn + 8.0 * nn * nn * nn + 8.0 * mm * nn);   // integers: exact in any order
+        }
+        if (tid == QSPACE - 1) {
+          int nnew = (int)v0, nsig = (int)v3;
+          if (nnew > nb_cap || v3 > MAXSIG) {
+            s_status |= STATUS_OVERFLOW;
+            nnew = 0;
+            nsig = 0;
+          }
+          s_nnew = nnew;
+          s_nsig = nsig;
+        }
+      }
     }
     __syncthreads();
     const int nnew = s_nnew;
