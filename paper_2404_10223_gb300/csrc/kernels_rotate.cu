@@ -936,6 +936,7 @@ __global__ void __launch_bounds__(C::threads, C::min_blocks) rotate_pairs_kernel
   __shared__ unsigned char sig_keep[MAXSIG];
   __shared__ short s_ord[QSPACE];                 // blocks of a gate: one per charge of the new bond
   __shared__ long long s_scan[QSPACE / 32][4];
+  __shared__ int s_tscan[C::warps][2], s_carry[2];
   __shared__ int s_nblk, s_nnew, s_total, s_nsig, s_keep, s_status, s_nbig;
   __shared__ float s_tscr[ROT_SLOTS];
   __shared__ int s_tbi[ROT_SLOTS], s_next_big, s_next_small;
@@ -1005,30 +1006,75 @@ __global__ void __launch_bounds__(C::threads, C::min_blocks) rotate_pairs_kernel
     double* Rt = D.work + D.work_off[a + 1];
     __syncthreads();
 
-    // ---- two-site tensor theta[l][k1][k2][r], charge-allowed blocks only
-    if (tid == 0) {
-      int nblk = 0, start = 0;
-      for (int sL = 0; sL < secL.nsec; ++sL)
-        for (int k1 = 0; k1 < 4; ++k1) {
+    // ---- two-site tensor theta[l][k1][k2][r], charge-allowed blocks only.  The
+    // block list (left sector, k1, k2 in that order) is built one item per thread,
+    // its start offsets from a prefix sum over the items, chunk by chunk.
+    {
+      const int nitems = secL.nsec * 16;
+      if (tid == 0) {
+        s_carry[0] = 0;
+        s_carry[1] = 0;
+      }
+      __syncthreads();
+      for (int base = 0; base < nitems; base += C::threads) {
+        const int it = base + tid;
+        int ex = 0, sz = 0, sL = 0, k1 = 0, k2 = 0, sM = -1, sR = -1;
+        if (it < nitems) {
+          sL = it >> 4;
+          k1 = (it >> 2) & 3;
+          k2 = it & 3;
           const int qM = qadd(secL.q[sL], local_charge(k1));
-          const int sM = qM < 0 ? -1 : lutM[qM];
-          if (sM < 0) continue;
-          for (int k2 = 0; k2 < 4; ++k2) {
+          sM = qM < 0 ? -1 : lutM[qM];
+          if (sM >= 0) {
             const int qR = qadd(qM, local_charge(k2));
-            const int sR = qR < 0 ? -1 : lutR[qR];
-            if (sR < 0) continue;
-            if (nblk < tb_cap) tb[nblk] = ThetaBlk{sL, sM, sR, k1, k2, start};
-            ++nblk;
-            start += secL.dim[sL] * secR.dim[sR];
-            s_flops += 2.0 * secL.dim[sL] * secM.dim[sM] * secR.dim[sR];
+            sR = qR < 0 ? -1 : lutR[qR];
+            if (sR >= 0) {
+              ex = 1;
+              sz = secL.dim[sL] * secR.dim[sR];
+            }
           }
         }
-      if (nblk > tb_cap) {
-        s_status |= STATUS_OVERFLOW;
-        nblk = (int)tb_cap;
+        int v0 = ex, v1 = sz;                      // inclusive scan within the warp
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int t0 = __shfl_up_sync(0xffffffffu, v0, o), t1 = __shfl_up_sync(0xffffffffu, v1, o);
+          if (lane >= o) {
+            v0 += t0;
+            v1 += t1;
+          }
+        }
+        if (lane == 31) {
+          s_tscan[warp][0] = v0;
+          s_tscan[warp][1] = v1;
+        }
+        __syncthreads();
+        v0 += s_carry[0];
+        v1 += s_carry[1];
+        for (int w = 0; w < warp; ++w) {
+          v0 += s_tscan[w][0];
+          v1 += s_tscan[w][1];
+        }
+        if (ex) {
+          const int idx = v0 - 1;
+          if (idx < tb_cap) tb[idx] = ThetaBlk{sL, sM, sR, k1, k2, v1 - sz};
+          atomicAdd(&s_flops, 2.0 * secL.dim[sL] * secM.dim[sM] * secR.dim[sR]);   // integers: exact in any order
+        }
+        __syncthreads();
+        if (tid == C::threads - 1) {               // the chunk's last item carries the running totals
+          s_carry[0] = v0;
+          s_carry[1] = v1;
+        }
+        __syncthreads();
       }
-      s_nblk = nblk;
-      s_total = start;
+      if (tid == 0) {
+        int nblk = s_carry[0];
+        if (nblk > tb_cap) {
+          s_status |= STATUS_OVERFLOW;
+          nblk = (int)tb_cap;
+        }
+        s_nblk = nblk;
+        s_total = s_carry[1];
+      }
     }
     __syncthreads();
     {
