@@ -399,9 +399,9 @@ def run_native(args):
     # DRAM bytes per launch from an ncu capture of the current kernel (profiles/), scaled from the
     # captured case to this launch by the units it processes; None where no capture exists.
     n_rot = sum(1 for i, j in pairs if i != j)
-    # rotate_pairs_kernel (1024-thread CTAs, 16-warp lead team): 10.14 MB read + 0.57 MB written by
+    # rotate_pairs_kernel (1024-thread CTAs, 12-warp lead team): 10.58 MB read + 0.57 MB written by
     # a launch of 2 rotated pairs of n14_chi128 (profiles/rotate_pairs_n14_small.md)
-    traffic_table = {("n14_chi128", "rotate_pairs_kernel"): 10.707e6 / 2 * n_rot}
+    traffic_table = {("n14_chi128", "rotate_pairs_kernel"): 11.154e6 / 2 * n_rot}
     traffic = traffic_table.get((w.name, top))
     t_ms, work, bound, peak, unit = kern[top]
     achieved = (work / (t_ms / 1e3)) / (1e12 if unit == "TFLOP/s" else 1e9) if t_ms > 0 else 0.0
