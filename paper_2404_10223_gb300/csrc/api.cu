@@ -550,6 +550,19 @@ void run_rotations(tnqe_ctx* c, const std::vector<std::pair<int, int>>& pairs, R
   }
   rb.per_small = per_small;
   upload(c, c->rot_small.p, small.data(), small.size());
+  // Launch order: the CTAs start in index order and a CTA's time grows with the
+  // rotated state's bond dimension, so when the pairs fill more than one wave of
+  // SMs the largest rotations go first (each descriptor carries all its pointers;
+  // the order changes no result).
+  {
+    std::vector<int> order(np);
+    for (int k = 0; k < np; ++k) order[k] = k;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int a, int b) { return chi_rot_of(c, rb.jj[a]) > chi_rot_of(c, rb.jj[b]); });
+    std::vector<RotDesc> launch_descs(np);
+    for (int t = 0; t < np; ++t) launch_descs[t] = descs[order[t]];
+    descs.swap(launch_descs);
+  }
   upload(c, c->rot_desc.p, descs.data(), sizeof(RotDesc) * np);
   record_event(c, c->pev[0]);
   CKL(launch_rotate(c->rot_desc.as<RotDesc>(), np, 0, c->stream));
