@@ -1826,8 +1826,15 @@ template <class F> void parallel_for(int n, F f) {
   for (auto& x : th) x.join();
 }
 
+// A state's site tensors on the host, sorted by charge, one allocation without
+// initialisation (every entry is written).
+struct HostTensor {
+  std::unique_ptr<double[]> p;
+  size_t n = 0;
+};
+
 void order_mps_host(int N, int na, int nb, const double* const* tensors, const int* bond_dims, const double* U,
-                    DevMps& m, std::vector<double>& host) {
+                    DevMps& m, HostTensor& out) {
   if (!tensors || !bond_dims || !U) throw Error(TNQE_ERR_ARG, "null argument");
   if (bond_dims[0] != 1 || bond_dims[N] != 1) throw Error(TNQE_ERR_ARG, "bond_dims[0] and bond_dims[N] must be 1");
   for (int b = 0; b <= N; ++b)
@@ -1840,64 +1847,68 @@ void order_mps_host(int N, int na, int nb, const double* const* tensors, const i
       if (std::fabs(acc - (p == q ? 1.0 : 0.0)) > 1e-12) throw Error(TNQE_ERR_ARG, "U is not orthogonal to 1e-12");
     }
   m.U.assign(U, U + (size_t)N * N);
-  // charges of every bond index, left to right
+  // charges of every bond index, left to right.  The charge of right index r is
+  // that of the first row (l, k) with weight in column r; the scan of a site
+  // stops once every column has one, and the parallel pass below checks every
+  // weighted entry against the charges.  The tolerance of a site is 1e-12 of
+  // its largest entry.
+  std::vector<double> amax(N, 0.0);
+  for (int s = 0; s < N; ++s)
+    if (!tensors[s]) throw Error(TNQE_ERR_ARG, "null site tensor");
+  parallel_for(N, [&](int s) {
+    const double* A = tensors[s];
+    const long long n = (long long)bond_dims[s] * 4 * bond_dims[s + 1];
+    double mx = 0.0;
+    for (long long x = 0; x < n; ++x) mx = std::max(mx, std::fabs(A[x]));
+    amax[s] = mx;
+  });
   std::vector<std::vector<int>> q(N + 1);
   q[0] = {0};
+  int noweight = -1;
   for (int s = 0; s < N; ++s) {
     const int cl = bond_dims[s], cr = bond_dims[s + 1];
     const double* A = tensors[s];
-    if (!A) throw Error(TNQE_ERR_ARG, "null site tensor");
-    double amax = 0.0;
-    for (long long x = 0; x < (long long)cl * 4 * cr; ++x) amax = std::max(amax, std::fabs(A[x]));
-    const double tol = 1e-12 * amax;
-    // the charge of right index r is that of the first row (l, k) with weight in
-    // column r; every other weighted entry of the column must carry the same.
-    // Rows are walked in order (contiguous memory), columns tracked in parallel.
+    const double tol = 1e-12 * amax[s];
     q[s + 1].assign(cr, -1);
-    for (int l = 0; l < cl; ++l)
+    int missing = cr;
+    for (int l = 0; l < cl && missing > 0; ++l)
+      for (int k = 0; k < 4 && missing > 0; ++k) {
+        const int qlk = (q[s][l] / QSTRIDE + (k & 1)) * QSTRIDE + q[s][l] % QSTRIDE + (k >> 1);
+        const double* row = A + ((size_t)l * 4 + k) * cr;
+        for (int r = 0; r < cr; ++r)
+          if (q[s + 1][r] < 0 && std::fabs(row[r]) > tol) {
+            q[s + 1][r] = qlk;
+            --missing;
+          }
+      }
+    if (missing > 0) {                            // reported below, after the block checks of the sites before
+      noweight = s;
+      break;
+    }
+  }
+  // the block-structure checks of the sites whose charges are known (all of
+  // them unless a bond index has no weight), then the errors in site order
+  const int nok = noweight >= 0 ? noweight : N;
+  std::vector<int> bad_block(N, 0);
+  parallel_for(nok, [&](int s) {
+    const int cl = bond_dims[s], cr = bond_dims[s + 1];
+    const double* A = tensors[s];
+    const double tol = 1e-12 * amax[s];
+    const std::vector<int>& qr0 = q[s + 1];
+    for (int l = 0; l < cl && !bad_block[s]; ++l)
       for (int k = 0; k < 4; ++k) {
         const int qlk = (q[s][l] / QSTRIDE + (k & 1)) * QSTRIDE + q[s][l] % QSTRIDE + (k >> 1);
         const double* row = A + ((size_t)l * 4 + k) * cr;
-        for (int r = 0; r < cr; ++r) {
-          if (!(std::fabs(row[r]) > tol)) continue;
-          if (q[s + 1][r] < 0) q[s + 1][r] = qlk;
-          else if (q[s + 1][r] != qlk)
-            throw Error(TNQE_ERR_ARG, "site " + std::to_string(s) + ": entry breaks the particle-number block structure");
-        }
-      }
-    for (int r = 0; r < cr; ++r)
-      if (q[s + 1][r] < 0) throw Error(TNQE_ERR_ARG, "site " + std::to_string(s) + ": bond index with no weight");
-  }
-  if (q[N][0] != na * QSTRIDE + nb) throw Error(TNQE_ERR_ARG, "state is not in the (n_alpha, n_beta) sector");
-  // left-orthonormal sites 0..N-2 (columns of different charge have disjoint support)
-  // (the Gram matrix of the columns accumulated row by row, contiguous in memory);
-  // the sites are independent and are checked on host threads
-  std::vector<int> bad(N, 0);
-  parallel_for(N - 1, [&](int s) {
-    const int cl = bond_dims[s], cr = bond_dims[s + 1];
-    const double* A = tensors[s];
-    std::vector<double> gram((size_t)cr * cr, 0.0);
-    std::vector<std::vector<int>> same(cr);        // columns of r's charge at or after r
-    for (int r1 = 0; r1 < cr; ++r1)
-      for (int r2 = r1; r2 < cr; ++r2)
-        if (q[s + 1][r1] == q[s + 1][r2]) same[r1].push_back(r2);
-    for (int lk = 0; lk < cl * 4; ++lk) {
-      const double* row = A + (size_t)lk * cr;
-      for (int r1 = 0; r1 < cr; ++r1) {
-        const double a1 = row[r1];
-        if (a1 == 0.0) continue;
-        double* g = gram.data() + (size_t)r1 * cr;
-        for (int r2 : same[r1]) g[r2] += a1 * row[r2];
-      }
-    }
-    for (int r1 = 0; r1 < cr; ++r1)
-      for (int r2 = r1; r2 < cr; ++r2) {
-        if (q[s + 1][r1] != q[s + 1][r2]) continue;
-        if (std::fabs(gram[(size_t)r1 * cr + r2] - (r1 == r2 ? 1.0 : 0.0)) > 1e-10) bad[s] = 1;
+        for (int r = 0; r < cr; ++r)
+          if (std::fabs(row[r]) > tol && qr0[r] != qlk) bad_block[s] = 1;
       }
   });
-  for (int s = 0; s + 1 < N; ++s)
-    if (bad[s]) throw Error(TNQE_ERR_ARG, "site " + std::to_string(s) + " is not left-orthonormal");
+  for (int s = 0; s < nok; ++s)
+    if (bad_block[s])
+      throw Error(TNQE_ERR_ARG, "site " + std::to_string(s) + ": entry breaks the particle-number block structure");
+  if (noweight >= 0)
+    throw Error(TNQE_ERR_ARG, "site " + std::to_string(noweight) + ": bond index with no weight");
+  if (q[N][0] != na * QSTRIDE + nb) throw Error(TNQE_ERR_ARG, "state is not in the (n_alpha, n_beta) sector");
   // sort every bond by charge (a gauge change: the state is unchanged)
   std::vector<std::vector<int>> perm(N + 1);
   m.dims.assign(bond_dims, bond_dims + N + 1);
@@ -1921,37 +1932,57 @@ void order_mps_host(int N, int na, int nb, const double* const* tensors, const i
       ++T.dim[T.nsec - 1];
     }
   }
-  host.clear();
   m.off.assign(N, 0);
-  {
-    size_t total = 0;
-    for (int s = 0; s < N; ++s) total += (size_t)bond_dims[s] * 4 * bond_dims[s + 1];
-    host.resize(total);                          // every entry is written below
+  size_t total = 0;
+  for (int s = 0; s < N; ++s) {
+    m.off[s] = (long long)total;
+    total += (size_t)bond_dims[s] * 4 * bond_dims[s + 1];
   }
-  {
-    size_t hoff = 0;
-    for (int s = 0; s < N; ++s) {
-      m.off[s] = (long long)hoff;
-      hoff += (size_t)bond_dims[s] * 4 * bond_dims[s + 1];
-    }
-  }
+  out.p.reset(new double[total]);                 // every entry is written below
+  out.n = total;
+  // one pass per site, sites on host threads: sites 0..N-2 left-orthonormal (the Gram matrix of the
+  // columns, block by block: columns of different charge have disjoint support);
+  // the site written in the sorted order, zero outside the blocks
+  std::vector<int> bad_orth(N, 0);
   parallel_for(N, [&](int s) {
     const int cl = bond_dims[s], cr = bond_dims[s + 1];
-    const size_t hoff = (size_t)m.off[s];
     const double* A = tensors[s];
+    const std::vector<int>& qr0 = q[s + 1];
+    if (s + 1 < N) {
+      std::vector<double> gram((size_t)cr * cr, 0.0);
+      std::vector<std::vector<int>> same(cr);      // columns of r's charge at or after r
+      for (int r1 = 0; r1 < cr; ++r1)
+        for (int r2 = r1; r2 < cr; ++r2)
+          if (qr0[r1] == qr0[r2]) same[r1].push_back(r2);
+      for (int lk = 0; lk < cl * 4; ++lk) {
+        const double* row = A + (size_t)lk * cr;
+        for (int r1 = 0; r1 < cr; ++r1) {
+          const double a1 = row[r1];
+          if (a1 == 0.0) continue;
+          double* g = gram.data() + (size_t)r1 * cr;
+          for (int r2 : same[r1]) g[r2] += a1 * row[r2];
+        }
+      }
+      for (int r1 = 0; r1 < cr && !bad_orth[s]; ++r1)
+        for (int r2 : same[r1])
+          if (std::fabs(gram[(size_t)r1 * cr + r2] - (r1 == r2 ? 1.0 : 0.0)) > 1e-10) bad_orth[s] = 1;
+    }
     std::vector<int> qr(cr);
-    for (int r = 0; r < cr; ++r) qr[r] = q[s + 1][perm[s + 1][r]];
+    for (int r = 0; r < cr; ++r) qr[r] = qr0[perm[s + 1][r]];
     const int* pr = perm[s + 1].data();
+    double* dst0 = out.p.get() + m.off[s];
     for (int l = 0; l < cl; ++l) {
       const int ql = q[s][perm[s][l]];
       for (int k = 0; k < 4; ++k) {
         const int qlk = (ql / QSTRIDE + (k & 1)) * QSTRIDE + ql % QSTRIDE + (k >> 1);
         const double* src = A + ((size_t)perm[s][l] * 4 + k) * cr;
-        double* dst = host.data() + hoff + ((size_t)l * 4 + k) * cr;
+        double* dst = dst0 + ((size_t)l * 4 + k) * cr;
         for (int r = 0; r < cr; ++r) dst[r] = (qlk == qr[r]) ? src[pr[r]] : 0.0;   // below-tolerance noise outside the blocks
       }
     }
   });
+  for (int s = 0; s + 1 < N; ++s)
+    if (bad_orth[s]) throw Error(TNQE_ERR_ARG, "site " + std::to_string(s) + " is not left-orthonormal");
 }
 
 // The Hamiltonian MPO of one state's basis, built on a host thread and packed
@@ -2028,16 +2059,19 @@ std::shared_ptr<MpoPack> build_mpo_pack(const double* h1, const double* eri, con
 // (one allocation, one copy) and start the build of its MPO on a host thread.
 void prepare_mps(tnqe_ctx* c, const double* const* tensors, const int* bond_dims, const double* U, DevMps& m) {
   const int N = c->N;
-  std::vector<double> host;
+  HostTensor host;
   order_mps_host(N, c->na, c->nb, tensors, bond_dims, U, m, host);
-  HostPack pk;
-  const size_t o_t = pk.add(host), o_off = pk.add(m.off), o_dims = pk.add(m.dims), o_sec = pk.add(m.sec);
+  HostPack pk;                                   // the small arrays, behind the tensors
+  const size_t o_off = pk.add(m.off), o_dims = pk.add(m.dims), o_sec = pk.add(m.sec);
+  const size_t tbytes = (host.n * sizeof(double) + 255) & ~(size_t)255;
   void* dev = nullptr;
-  CK(cudaMalloc(&dev, pk.h.size()));
+  CK(cudaMalloc(&dev, tbytes + pk.h.size()));
   m.owned.push_back(dev);
-  CK(cudaMemcpy(dev, pk.h.data(), pk.h.size(), cudaMemcpyHostToDevice));
   unsigned char* base = static_cast<unsigned char*>(dev);
-  m.d_t = reinterpret_cast<double*>(base + o_t);
+  CK(cudaMemcpy(base, host.p.get(), host.n * sizeof(double), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(base + tbytes, pk.h.data(), pk.h.size(), cudaMemcpyHostToDevice));
+  base += tbytes;
+  m.d_t = reinterpret_cast<double*>(static_cast<unsigned char*>(dev));
   m.d_off = reinterpret_cast<long long*>(base + o_off);
   m.d_dims = reinterpret_cast<int*>(base + o_dims);
   m.d_sec = reinterpret_cast<SectorTable*>(base + o_sec);
@@ -2231,7 +2265,7 @@ tnqe_status tnqe_check_mps(int N, int n_alpha, int n_beta, const double* const* 
       return TNQE_ERR_ARG;
     }
     DevMps m;
-    std::vector<double> host;
+    HostTensor host;
     order_mps_host(N, n_alpha, n_beta, tensors, bond_dims, U, m, host);
     put("");
     return TNQE_OK;
