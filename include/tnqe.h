@@ -167,15 +167,17 @@ tnqe_status tnqe_create(const double* h1, const double* eri, int N, int n_alpha,
  * last site, Eq. A3) to 1e-10, and every bond index must carry a definite
  * (n_alpha, n_beta) charge: A[l,k,r] may be nonzero (above 1e-12 of the
  * site's largest entry) only when q(l) + q(k) = q(r), with the last bond at
- * (n_alpha, n_beta).  Violations return TNQE_ERR_ARG.  Uploads the tensors and
- * starts the build of the Hamiltonian MPO in basis U on a host thread; the
- * first tnqe_matrix_elements call with this state as a bra waits for that
- * build while its rotations run on the GPU, and uploads the MPO (an error of
- * the build is reported by that call). */
+ * (n_alpha, n_beta).  Violations return TNQE_ERR_ARG.  Uploads the tensors
+ * (synchronously).  The Hamiltonian MPO in basis U is built on a host thread
+ * that the first call needing it starts: tnqe_matrix_elements with this state
+ * as a bra starts the build after enqueueing its rotations, waits for it while
+ * the rotation kernel runs, and uploads the MPO (an error of the build is
+ * reported by that call). */
 tnqe_status tnqe_add_mps(tnqe_ctx* ctx, const double* const* tensors, const int* bond_dims,
                          const double* U, int* mps_id);
 
-/* Drop every state (device buffers are kept for reuse by later adds). */
+/* Drop every state and free its device buffers (waits for the context's
+ * stream and for any MPO build still running). */
 tnqe_status tnqe_reset_mps(tnqe_ctx* ctx);
 
 /* Rotate MPS j into basis i (Eq. 11 with truncation, Sec. II D) and keep the
