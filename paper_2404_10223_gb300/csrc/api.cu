@@ -262,6 +262,8 @@ struct tnqe_ctx {
   std::vector<int> exact_dim;            // N + 1: full sector-space dimension per bond
   cudaStream_t stream = nullptr;
   bool own_stream = false;
+  void* stage = nullptr;                 // pinned staging of tnqe_add_mps (stage_cap doubles)
+  size_t stage_cap = 0;
   std::vector<std::unique_ptr<DevMps>> mps;
   std::map<std::pair<int, int>, std::unique_ptr<PairPlan>> plans;
   std::vector<void*> plan_arenas;        // device memory of the plans, one allocation per batch
@@ -1832,7 +1834,10 @@ template <class F> void parallel_for(int n, F f) {
 // initialisation (every entry is written).
 struct HostTensor {
   std::unique_ptr<double[]> p;
+  double* ext = nullptr;                 // a caller's buffer of ext_cap doubles, used when it is large enough
+  size_t ext_cap = 0;
   size_t n = 0;
+  double* data() { return ext && ext_cap >= n ? ext : p.get(); }
 };
 
 void order_mps_host(int N, int na, int nb, const double* const* tensors, const int* bond_dims, const double* U,
@@ -1940,8 +1945,8 @@ void order_mps_host(int N, int na, int nb, const double* const* tensors, const i
     m.off[s] = (long long)total;
     total += (size_t)bond_dims[s] * 4 * bond_dims[s + 1];
   }
-  out.p.reset(new double[total]);                 // every entry is written below
   out.n = total;
+  if (!(out.ext && out.ext_cap >= total)) out.p.reset(new double[total]);   // every entry is written below
   // one pass per site, sites on host threads: sites 0..N-2 left-orthonormal (the Gram matrix of the
   // columns, block by block: columns of different charge have disjoint support);
   // the site written in the sorted order, zero outside the blocks
@@ -1972,7 +1977,7 @@ void order_mps_host(int N, int na, int nb, const double* const* tensors, const i
     std::vector<int> qr(cr);
     for (int r = 0; r < cr; ++r) qr[r] = qr0[perm[s + 1][r]];
     const int* pr = perm[s + 1].data();
-    double* dst0 = out.p.get() + m.off[s];
+    double* dst0 = out.data() + m.off[s];
     for (int l = 0; l < cl; ++l) {
       const int ql = q[s][perm[s][l]];
       for (int k = 0; k < 4; ++k) {
@@ -2070,7 +2075,21 @@ void start_mpo(tnqe_ctx* c, DevMps& m) {
 
 void prepare_mps(tnqe_ctx* c, const double* const* tensors, const int* bond_dims, const double* U, DevMps& m) {
   const int N = c->N;
+  // the sorted tensors go to a pinned staging buffer of the context (grown when
+  // too small), so that the upload is one direct copy
+  size_t need = 0;
+  for (int s = 0; bond_dims && s < N; ++s)      // (order_mps_host reports bad arguments)
+    need += (size_t)std::min(std::max(bond_dims[s], 0), 256) * 4 * std::min(std::max(bond_dims[s + 1], 0), 256);
+  if (need > c->stage_cap) {
+    if (c->stage) cudaFreeHost(c->stage);
+    c->stage = nullptr;
+    c->stage_cap = 0;
+    if (cudaHostAlloc(&c->stage, need * sizeof(double), cudaHostAllocDefault) == cudaSuccess) c->stage_cap = need;
+    else c->stage = nullptr;                    // pageable memory then
+  }
   HostTensor host;
+  host.ext = static_cast<double*>(c->stage);
+  host.ext_cap = c->stage_cap;
   order_mps_host(N, c->na, c->nb, tensors, bond_dims, U, m, host);
   HostPack pk;                                   // the small arrays, behind the tensors
   const size_t o_off = pk.add(m.off), o_dims = pk.add(m.dims), o_sec = pk.add(m.sec);
@@ -2079,7 +2098,7 @@ void prepare_mps(tnqe_ctx* c, const double* const* tensors, const int* bond_dims
   CK(cudaMalloc(&dev, tbytes + pk.h.size()));
   m.owned.push_back(dev);
   unsigned char* base = static_cast<unsigned char*>(dev);
-  CK(cudaMemcpy(base, host.p.get(), host.n * sizeof(double), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(base, host.data(), host.n * sizeof(double), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(base + tbytes, pk.h.data(), pk.h.size(), cudaMemcpyHostToDevice));
   base += tbytes;
   m.d_t = reinterpret_cast<double*>(static_cast<unsigned char*>(dev));
@@ -2753,6 +2772,8 @@ void tnqe_destroy(tnqe_ctx* c) {
   c->rot_meta.release();
   c->rot_small.release();
   c->rot_desc.release();
+  if (c->stage) cudaFreeHost(c->stage);
+  c->stage = nullptr;
   c->con_ws.release();
   c->con_desc.release();
   c->con_out.release();
