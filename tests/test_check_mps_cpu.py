@@ -67,3 +67,29 @@ def test_bond_dimensions_at_the_ends():
 def test_bad_electron_numbers():
     w, ts, U = _state()
     assert tnqe.tnqe_check_mps(ts, U, 7, 0)[0] == 1
+
+
+def test_errors_are_reported_in_site_order():
+    """A block-structure violation at an early site is reported before a column
+    without weight at a later site and before a non-orthonormal site, and the
+    site number in the message is the earliest offending one."""
+    w, ts, U = _state()
+    A = ts[1]
+    l, k, r = [int(x[0]) for x in np.nonzero(A == 0.0)]
+    A[l, k, r] = 0.3                                          # site 1: outside the blocks
+    ts[3][:, :, 0] = 0.0                                      # site 3: a bond index with no weight
+    ts[4] *= 1.5                                              # site 4: not left-orthonormal
+    st, msg = tnqe.tnqe_check_mps(ts, U, w.n_alpha, w.n_beta)
+    assert st == 1 and "block structure" in msg and "site 1" in msg
+    w, ts, U = _state()
+    ts[2][:, :, 0] = 0.0                                      # site 2: no weight
+    ts[1] *= 1.5                                              # site 1: not left-orthonormal (checked later)
+    st, msg = tnqe.tnqe_check_mps(ts, U, w.n_alpha, w.n_beta)
+    assert st == 1 and "no weight" in msg and "site 2" in msg
+
+
+def test_states_of_the_benchmark_workload_are_valid():
+    """The N = 14, chi = 128 states pass (the sites are checked on host threads)."""
+    w = inputs.workload("n14_chi128")
+    for m in w.mps[:4]:
+        assert tnqe.tnqe_check_mps(m.tensors, m.U, w.n_alpha, w.n_beta) == (0, "")
